@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark: decoded GB/s of canonical-Huffman decoding of a 512^3 field of
+Lorenzo quantization codes on GB300, through the library's C ABI.
+
+One step = one hd_decode of the whole field (decode-table kernel + persistent
+gap-array decode kernel), inputs resident in HBM, L2 flushed between steps.
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead (bounded samples of the same workload on the host cores).
+
+Multi-GPU (torchrun): every rank decodes its own field of the same shape
+(replicas, no collective on the data path); value = all ranks' symbols / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "decoded GB/s & % HBM roofline; batched/served vs per-field; p50/p99 latency"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def workload_codes(side: int, seed: int):
+    import synth
+    return synth.field3d_codes(side, rel_eb=1e-4, noise=0.01, seed=seed)
+
+
+def workload_desc(side: int) -> str:
+    return (f"{side}^3 float32 field (64 Fourier modes, 1/k^2 amplitude, +1% Gaussian noise), "
+            f"3D Lorenzo, rel. error bound 1e-4, radius 512 -> {side**3} uint16 codes; "
+            f"canonical Huffman (max 32 bits), MSB-first uint32 stream, S=128, uint8 gap array")
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_2201_09118_gb300", "csrc")
+    for name in ("decode_gap.cu", "decode_common.cuh", "common.cuh"):
+        with open(os.path.join(cs, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, n_codes: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        e = d[kernel]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch"]) * n_codes / float(e["n_codes"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(codes: np.ndarray, target_s: float = 12.0):
+    """The oracle's sequential bit-by-bit decoder on a prefix sample of the
+    same field (single host thread)."""
+    import oracle
+    n = min(codes.size, 1 << 24)
+    x = codes[:n]
+    c = oracle.compress(x, 1024, S=128)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        out = oracle.decode(c["words"], c["nbits"], c["codes"], c["lengths"], n_cap=n)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= target_s or reps >= 8:
+            break
+    assert np.array_equal(out, x)
+    gbps = 2.0 * n * reps / el / 1e9
+    return {"value": gbps, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} codes of the field ({c['nbits']} bits), decoded {reps}x "
+                      f"sequentially by the oracle's bit-by-bit tree walk, 1 host thread",
+            "seconds": el}
+
+
+def run_reference(args):
+    """CPU oracle arm: each step decodes a bounded sample of the workload."""
+    import oracle
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    side = args.side
+    codes = workload_codes(side, seed=1001)
+    n = min(codes.size, 1 << 22)
+    x = codes[:n]
+    c = oracle.compress(x, 1024, S=128)
+    for _ in range(args.warmup):
+        oracle.decode(c["words"], c["nbits"], c["codes"], c["lengths"], n_cap=n)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        out = oracle.decode(c["words"], c["nbits"], c["codes"], c["lengths"], n_cap=n)
+        times.append(time.perf_counter() - t0)
+    assert np.array_equal(out, x)
+    total = sum(times)
+    value = 2.0 * n * args.steps / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+        "config": {"workload": workload_desc(side), "sample_codes": n,
+                   "parallelism": "single host thread"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {n} codes of the field per step"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    from paper_2201_09118_gb300 import hd
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    side = args.side
+    codes = workload_codes(side, seed=1001 + rank)
+    n = codes.size
+    lengths = hd.hd_build_codebook(codes, 1024, 32)
+    enc = hd.hd_encode(codes, lengths, 128)
+    field = hd.DeviceField.upload(enc, lengths, n, device=f"cuda:{dev}")
+    field_ss = hd.DeviceField(field.words, field.nbits, None, 128, field.lengths, 1024, n)
+    out = torch.empty(n, dtype=torch.int16, device=f"cuda:{dev}")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
+    ctx = hd.Context(dev)
+    if args.threads or args.window or args.lut_bits:
+        ctx.set_config(threads=args.threads, window=args.window, lut_bits=args.lut_bits)
+    stream = torch.cuda.current_stream()
+
+    # correctness of the timed configuration (round trip against the codes)
+    ctx.decode(field, out, stream)
+    st = ctx.status(stream)
+    ok = st == 0 and np.array_equal(out.cpu().numpy().view(np.uint16), codes)
+    if not ok:
+        print(json.dumps({"error": f"decode mismatch or status {st}"}), flush=True)
+        return 1
+
+    def timed(f, steps, warmup):
+        for _ in range(warmup):
+            ctx.decode(f, out, stream)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.kernel_time()  # clear
+        l0 = ctx.launch_count()
+        evs = []
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.decode(f, out, stream)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        launches = ctx.launch_count() - l0
+        kms, kl = ctx.kernel_time()
+        ctx.profile(False)
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        st = ctx.status(stream)
+        return ms, kms, kl, launches, st
+
+    sampler = ClockSampler(dev)
+    sampler.start()
+    ms, kms, kl, launches, st = timed(field, args.steps, args.warmup)
+    clocks = sampler.stop()
+    if st != 0:
+        print(json.dumps({"error": f"decode status {st} in timed region"}), flush=True)
+        return 1
+    ms_ss, kms_ss, kl_ss, _, st_ss = timed(field_ss, max(3, args.steps // 2), 2)
+
+    if dist:
+        t = torch.tensor([ms, ms_ss], dtype=torch.float64, device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_ss = float(t[0]), float(t[1])
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    words_h = torch.from_numpy(enc["words"].view(np.int32)).pin_memory()
+    gap_h = torch.from_numpy(enc["gap"]).pin_memory()
+    len_h = torch.from_numpy(lengths).pin_memory()
+    out_h = torch.empty(n, dtype=torch.int16).pin_memory()
+    e2e_times = []
+    e2e_steps = max(3, args.steps // 2)
+    for k in range(2 + e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc = ctx.decode_host_ptrs(words_h.data_ptr(), enc["nwords"], enc["nbits"],
+                                  gap_h.data_ptr(), 128, len_h.data_ptr(), 1024, n,
+                                  out_h.data_ptr(), stream)
+        t1 = time.perf_counter()
+        if rc != 0:
+            print(json.dumps({"error": f"hd_decode_host status {rc}"}), flush=True)
+            return 1
+        if k >= 2:
+            e2e_times.append(t1 - t0)
+    assert np.array_equal(out_h.numpy().view(np.uint16), codes)
+    e2e_gbps = 2.0 * n / statistics.median(e2e_times) / 1e9
+    if dist:
+        t = torch.tensor([e2e_gbps], dtype=torch.float64, device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MIN)
+        e2e_gbps = float(t[0]) * world
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    nbytes_alg = (enc["nbits"] + 7) // 8 + enc["nsub"] + 2 * n
+    kernel_ms = kms / max(1, kl)
+    achieved = nbytes_alg / (kernel_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    value = 2.0 * n * args.steps * world / (ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+        "config": {"workload": workload_desc(side), "n_codes": n,
+                   "bits_per_code": enc["nbits"] / n, "strategy": "gap array",
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "parallelism": f"replicas x{world}", "launch": ctx.get_config()},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": recorded_traffic("decode_gap", n),
+                     "peak_kind": peak_kind, "kernel": "k_decode_gap",
+                     "kernel_ms": kernel_ms, "algorithmic_bytes": nbytes_alg},
+        "e2e": {"value": e2e_gbps, "unit": "GB/s",
+                "h2d_bytes_per_step": int(enc["nwords"] * 4 + enc["nsub"] + 1024),
+                "d2h_bytes_per_step": int(2 * n)},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "selfsync": {"value": 2.0 * n * max(3, args.steps // 2) * world / (ms_ss * 1e-3) / 1e9,
+                     "unit": "GB/s", "kernel_ms": kms_ss / max(1, kl_ss), "status": st_ss},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(codes)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=512)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--window", type=int, default=0)
+    ap.add_argument("--lut-bits", dest="lut_bits", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,178 @@
+/*
+ * hd.h -- C ABI of the GB300 (sm_103a) Huffman decoder for error-bounded lossy
+ * compression codes.
+ *
+ * The library decodes canonical-Huffman streams of uint16 quantization codes
+ * (the Lorenzo residues a cuSZ-style compressor produces) from a dense,
+ * most-significant-bit-first uint32 bitstream into a uint16 array on the GPU.
+ * It implements the two start-point strategies the paper (Rivera et al.,
+ * "Optimizing Huffman Decoding for Error-Bounded Lossy Compression on GPUs",
+ * IPDPS 2022) optimises:
+ *   - gap arrays (Sec. III-C): one byte per subsequence tells each thread
+ *     where its first codeword starts;
+ *   - self-synchronisation (Sec. III-B, Sec. IV-A): threads start at evenly
+ *     spaced positions and agree on true codeword boundaries.
+ * Output offsets come from a prefix sum of per-subsequence codeword counts
+ * (Sec. III-B2 step 3) and symbols are staged in shared memory before
+ * coalesced stores (Sec. IV-B, Algorithm 1).
+ *
+ * Stream format (shared by hd_encode and every decode entry point):
+ *   - bit b of the stream is bit 31 - (b mod 32) of unit floor(b / 32);
+ *   - `nbits` valid bits, then zero padding to a multiple of the subsequence
+ *     size S bits, then one zero guard unit:
+ *     nwords = ceil(nbits / S) * S / 32 + 1 (S a multiple of 32);
+ *   - codewords are canonical (RFC 1951 Sec. 3.2.2 assignment) for the code
+ *     lengths `lengths[alphabet]` (0 = symbol absent, at most 32 bits);
+ *   - gap array (optional): gap[i] = (first codeword boundary at or after
+ *     bit i*S) - i*S, one uint8 per subsequence, in [0, 31].  The boundaries
+ *     are the codeword starts and the stream end.  The paper's example
+ *     [0, 0, -2, -1] (Sec. III-C) uses the signed offset to the codeword that
+ *     straddles the boundary; the two conventions differ by that codeword's
+ *     length.
+ *
+ * Ownership: every pointer stays owned by the caller.  Device pointers must
+ * stay valid until the work queued on the given stream has finished.
+ * Errors are returned as negative status codes; no exception crosses the ABI.
+ * A context may be used from several host threads (calls are serialised by
+ * an internal lock) but decodes queued on one context must not overlap on the
+ * device: use one context per concurrently running stream.
+ */
+#ifndef HD_H
+#define HD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define HD_OK 0
+#define HD_PENDING 1        /* serve: request not finished yet */
+#define HD_ERR_ARG (-1)     /* invalid argument, size or alignment */
+#define HD_ERR_CAPACITY (-2)/* output buffer too small (required sizes reported) */
+#define HD_ERR_SYMBOL (-3)  /* input symbol outside the alphabet or without code */
+#define HD_ERR_CORRUPT (-4) /* stream is no valid encoding of n symbols */
+#define HD_ERR_NOSYNC (-5)  /* self-synchronisation did not converge in its cap */
+#define HD_ERR_TIMEOUT (-6) /* a device-side wait gave up (look-back chain) */
+#define HD_ERR_CUDA (-7)    /* a CUDA runtime call failed */
+#define HD_ERR_NOMEM (-8)   /* host or device allocation failed / over budget */
+#define HD_ERR_BUSY (-9)    /* serve: queue full or server stopped */
+
+/* ---- host-side codebook construction and encoding (test-input generation) */
+
+typedef struct hd_stream_info {
+  uint64_t nbits;  /* valid bits in the stream */
+  uint64_t nwords; /* uint32 units including padding and the guard unit */
+  uint64_t nsub;   /* subsequences = gap entries = ceil(nbits / S) */
+} hd_stream_info;
+
+/* Code lengths of an optimal prefix code for the histogram of codes[0..n)
+ * (Huffman's construction, Sec. II-B), limited to max_len bits with
+ * package-merge when the Huffman tree is deeper.  A single used symbol gets
+ * length 1.  Host memory.  Errors: HD_ERR_ARG if alphabet is not in [2, 65536]
+ * or max_len not in [1, 32] or more than 2^max_len symbols are used;
+ * HD_ERR_SYMBOL if a code is >= alphabet. */
+int hd_build_codebook(const uint16_t* codes, uint64_t n, uint32_t alphabet, uint32_t max_len,
+                      uint8_t* lengths_out);
+
+/* Canonical-Huffman encodes codes[0..n) into the stream format above, with
+ * subsequences of subseq_bits (64, 128 or 256) and, when gap_out is not NULL,
+ * the gap array.  Host memory.  `info` always receives the required sizes.
+ * Errors: HD_ERR_CAPACITY if words_cap < info->nwords or (gap_out != NULL and)
+ * gap_cap < info->nsub; HD_ERR_SYMBOL for a symbol with length 0 or outside
+ * the alphabet; HD_ERR_ARG for an invalid length table (Kraft sum > 1). */
+int hd_encode(const uint16_t* codes, uint64_t n, const uint8_t* lengths, uint32_t alphabet,
+              uint32_t subseq_bits, uint32_t* words_out, uint64_t words_cap, uint8_t* gap_out,
+              uint64_t gap_cap, hd_stream_info* info);
+
+/* ---- device context ---------------------------------------------------- */
+
+typedef struct hd_ctx hd_ctx;
+
+/* Creates a context bound to CUDA device `device`.  The context owns its
+ * device workspace (look-back states, decode tables, error words), which grows
+ * on demand with cudaMalloc outside of any decode call's device work. */
+int hd_ctx_create(int device, hd_ctx** out);
+int hd_ctx_destroy(hd_ctx* ctx);
+
+/* One encoded field.  All pointers are device pointers for hd_decode and
+ * hd_decode_batch, host pointers for hd_decode_host. */
+typedef struct hd_field {
+  const uint32_t* words;    /* stream, nwords units, 16-byte aligned */
+  uint64_t nwords;          /* must be >= ceil(nbits / S) * S / 32 + 1 */
+  uint64_t nbits;           /* valid bits */
+  const uint8_t* gap;       /* gap array or NULL (=> self-synchronisation) */
+  uint32_t subseq_bits;     /* S the stream/gap array was written with: 64, 128, 256 */
+  const uint8_t* lengths;   /* code lengths [alphabet] */
+  uint32_t alphabet;        /* 2 .. 65536 */
+  uint64_t n;               /* number of symbols encoded in the stream */
+} hd_field;
+
+/* Launch shape (0 = library default / autotuned choice). */
+typedef struct hd_config {
+  uint32_t subseq_bits; /* decoder subsequence: a multiple of the field's S, <= 256 */
+  uint32_t threads;     /* threads per block = subsequences per tile: 128, 256, 512 */
+  uint32_t window;      /* shared-memory output window in symbols (Alg. 1 buffer) */
+  uint32_t lut_bits;    /* first-level decode-table index bits, 8 .. 13 */
+  uint32_t tiles_per_unit; /* tiles per look-back step (work unit), 1 .. 16 */
+} hd_config;
+
+/* Sets the launch shape used by later decodes on this context (NULL resets to
+ * defaults).  HD_ERR_ARG for values outside the ranges above. */
+int hd_set_config(hd_ctx* ctx, const hd_config* cfg);
+int hd_get_config(hd_ctx* ctx, hd_config* cfg);
+
+/* Decodes field `f` into d_out[0 .. f->n) on `stream` (a cudaStream_t, NULL =
+ * legacy default stream).  Asynchronous: argument errors are returned
+ * immediately; stream errors are recorded on the device and returned by
+ * hd_status.  With a gap array the start of every subsequence is read from
+ * it; without one it is found by self-synchronisation.  d_out must be 2-byte
+ * aligned and hold f->n elements; nothing outside it is written, even for a
+ * corrupt stream. */
+int hd_decode(hd_ctx* ctx, const hd_field* f, uint16_t* d_out, void* stream);
+
+/* Waits for `stream` and returns the status of the last hd_decode /
+ * hd_sync_points / hd_decode_batch queued on this context: HD_OK,
+ * HD_ERR_CORRUPT, HD_ERR_NOSYNC, HD_ERR_TIMEOUT or HD_ERR_CUDA. */
+int hd_status(hd_ctx* ctx, void* stream);
+
+/* Self-synchronisation only (Sec. III-B2 steps 1-2): computes the gap array
+ * gap_out[0 .. ceil(nbits/S)) of field `f` (whose `gap` is ignored) from the
+ * bitstream, with S = f->subseq_bits.  Device pointers, asynchronous, status
+ * via hd_status. */
+int hd_sync_points(hd_ctx* ctx, const hd_field* f, uint8_t* gap_out, void* stream);
+
+/* Decodes nf independent fields (device pointers, own codebooks) in one
+ * persistent launch; d_outs[i] receives field i.  Per-field status via
+ * hd_batch_status. */
+int hd_decode_batch(hd_ctx* ctx, const hd_field* fs, uint32_t nf, uint16_t* const* d_outs,
+                    void* stream);
+/* Waits for `stream`; status[i] = status of field i of the last batch. Returns
+ * the first non-OK status or HD_OK. */
+int hd_batch_status(hd_ctx* ctx, int32_t* status, uint32_t nf, void* stream);
+
+/* Host-buffer decode: `f` holds HOST pointers (pinned memory is fastest),
+ * host_out receives f->n symbols.  Copies the stream, gap array and lengths
+ * to context-owned device buffers, decodes and copies the symbols back, all
+ * on `stream`; returns when done with the decode status. */
+int hd_decode_host(hd_ctx* ctx, const hd_field* f, uint16_t* host_out, void* stream);
+
+/* Kernel timing: when enabled, the context records CUDA events around every
+ * main decode kernel it launches.  hd_kernel_time waits for them and returns
+ * the summed device time in milliseconds and the launch count, then clears. */
+int hd_profile(hd_ctx* ctx, int enable);
+int hd_kernel_time(hd_ctx* ctx, double* ms, uint64_t* launches);
+
+/* Number of kernel launches the context has issued since creation. */
+uint64_t hd_launch_count(hd_ctx* ctx);
+
+/* Library version string. */
+const char* hd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HD_H */

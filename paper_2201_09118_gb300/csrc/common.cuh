@@ -1,0 +1,99 @@
+// common.cuh -- device data structures shared by the decode-table kernel and
+// the decode kernels of the GB300 Huffman decoder.
+#pragma once
+
+#include <cstdint>
+
+namespace hd {
+
+constexpr uint32_t kMaxCodeLen = 32;
+constexpr uint32_t kMaxTilesPerUnit = 16;
+constexpr uint32_t kTableHeaderBytes = 512;
+
+// Decode-table header, written by the table kernel, followed in memory by the
+// first-level table (uint32[2^K]) at kTableHeaderBytes and then by the symbols
+// sorted by (code length, symbol) (uint16[alphabet]).
+//
+// Canonical codes occupy, for each length L, the left-aligned 32-bit interval
+//   [first[L] << (32-L), (first[L] + count[L]) << (32-L)),
+// and these intervals are consecutive in L, so the length of the codeword at a
+// left-aligned 32-bit window w is the smallest L with w < end[L], and its rank
+// among codes sorted by (length, symbol) is (w >> (32-L)) - first[L] + start[L].
+struct TableHeader {
+  uint32_t status;   // 0 = valid length table; else bad (Kraft sum > 1, length > 32)
+  uint32_t maxlen;   // longest code length in use (0 if no symbol is used)
+  uint32_t nused;    // symbols with a code
+  uint32_t K;        // first-level index bits
+  uint64_t end[34];  // end[L]: exclusive left-aligned limit of codes of length <= L
+  uint32_t base[34]; // start[L] - first[L] (mod 2^32): rank = (w >> (32-L)) + base[L]
+};
+static_assert(sizeof(TableHeader) <= kTableHeaderBytes, "table header too large");
+
+// First-level entry: bit 31 clear -> (len << 16) | symbol with len <= K;
+// bit 31 set -> the code is longer than K bits (or the prefix is no code):
+// bits 0..7 hold the smallest length a code with this prefix can have (33 if
+// none can), and the length is found by walking end[] from there.
+constexpr uint32_t kLongFlag = 0x80000000u;
+
+// Per-field work description (device memory for batches, a kernel parameter
+// for single fields).
+struct FieldDesc {
+  const uint32_t* words;   // bitstream
+  uint64_t nwords;         // units readable in `words`
+  uint64_t nbits;          // valid bits
+  uint64_t nsub;           // decoder subsequences = ceil(nbits / S)
+  const uint8_t* gap;      // gap array of the stream (NULL: self-synchronisation)
+  uint32_t gap_stride;     // decoder S / stream S
+  uint32_t alphabet;
+  const uint8_t* lengths;  // code lengths [alphabet]
+  const TableHeader* table;// decode table built from `lengths`
+  uint16_t* out;           // decoded symbols [n]
+  uint64_t n;              // expected symbol count
+  uint64_t unit_begin;     // index of this field's first work unit in the launch
+  uint64_t nunits;         // work units of this field
+  uint32_t* err;           // error bits of this field
+  uint8_t* gap_out;        // sync-point mode: gap array written here
+};
+
+// Error bits (per field).
+enum : uint32_t {
+  kErrCode = 1u,     // a bit pattern that is no codeword
+  kErrGap = 2u,      // gap entry out of range or not at a codeword boundary
+  kErrCount = 4u,    // decoded symbol count differs from n
+  kErrTimeout = 8u,  // a look-back wait gave up
+  kErrNoSync = 16u,  // self-synchronisation hit its round cap
+  kErrTable = 32u,   // invalid code-length table
+};
+
+struct DecodeParams {
+  FieldDesc f0;             // the field when nfields == 1
+  const FieldDesc* fields;  // device array when nfields > 1
+  uint32_t nfields;
+  uint32_t K;               // first-level table bits for this launch
+  uint32_t window;          // shared-memory output window, symbols (Alg. 1 buffer)
+  uint32_t sync_only;       // 1: write gap arrays, do not decode
+  uint32_t M;               // tiles of B subsequences per work unit (1 .. kMaxTilesPerUnit)
+  uint32_t pad0;
+  uint64_t total_units;
+  uint64_t* unit_state;     // look-back state per work unit (zeroed before launch)
+  uint32_t* ticket;         // dynamic work-unit counter (zeroed before launch)
+  uint32_t* abort_flag;     // set when any wait times out (zeroed before launch)
+  uint64_t timeout_ns;      // per-wait limit
+};
+
+struct PrepParams {
+  FieldDesc f0;
+  const FieldDesc* fields;
+  uint32_t nfields;
+  uint32_t K;
+  uint4* zero_ptr;          // region cleared before the decode kernel
+  uint64_t zero_vec;        // its size in 16-byte vectors
+  uint32_t zero_blocks;
+};
+
+// Look-back state word: flag in bits 62..63, value in bits 0..61.
+constexpr uint64_t kStateAgg = 1ull << 62;
+constexpr uint64_t kStateInc = 2ull << 62;
+constexpr uint64_t kStateValMask = (1ull << 62) - 1;
+
+}  // namespace hd

@@ -1,0 +1,312 @@
+// decode_common.cuh -- device building blocks of the decode kernels:
+// bitstream staging, decode-table lookups, block scans, the decoupled
+// look-back over tiles and the shared-memory staged output window.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace hd {
+namespace dev {
+
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint4 ldg_v4(const uint32_t* p) {
+  return __ldg(reinterpret_cast<const uint4*>(p));
+}
+__device__ __forceinline__ uint2 ldg_v2(const uint32_t* p) {
+  return __ldg(reinterpret_cast<const uint2*>(p));
+}
+
+// Decode tables as seen by one block: first level in shared memory, the
+// per-length limits in shared memory, the sorted symbols in global memory
+// (only codes longer than K bits read them).
+struct Tables {
+  const uint32_t* lut;
+  const uint64_t* end;
+  const uint32_t* base;
+  const uint16_t* sorted;
+  uint32_t maxlen;
+  uint32_t shift;  // 32 - K
+};
+
+// Bits [p, p + 32) of a staged subsequence.  Column `col` holds the
+// subsequence's units at stride B (unit k at col[k * B]), so the 32 lanes of a
+// warp always read 32 distinct banks whatever their positions.
+template <int B>
+__device__ __forceinline__ uint32_t peek(const uint32_t* col, uint32_t p) {
+  const uint32_t k = p >> 5;
+  return __funnelshift_l(col[(k + 1) * B], col[k * B], p);
+}
+
+// Length of the codeword at window w (long codes walk the canonical limits).
+// An invalid bit pattern sets `bad` and counts as one bit, so a decoder that
+// started at a wrong position still advances.
+__device__ __forceinline__ uint32_t code_len(const Tables& T, uint32_t w, bool& bad) {
+  const uint32_t e = T.lut[w >> T.shift];
+  if (!(e & kLongFlag)) return e >> 16;
+  uint32_t L = e & 0xFFu;
+  while (L <= T.maxlen && static_cast<uint64_t>(w) >= T.end[L]) ++L;
+  if (L > T.maxlen) {
+    bad = true;
+    return 1;
+  }
+  return L;
+}
+
+// Length and symbol of the codeword at window w.
+__device__ __forceinline__ uint32_t code_sym(const Tables& T, uint32_t w, uint32_t& sym,
+                                             bool& bad) {
+  const uint32_t e = T.lut[w >> T.shift];
+  if (!(e & kLongFlag)) {
+    sym = e & 0xFFFFu;
+    return e >> 16;
+  }
+  uint32_t L = e & 0xFFu;
+  while (L <= T.maxlen && static_cast<uint64_t>(w) >= T.end[L]) ++L;
+  if (L > T.maxlen) {
+    bad = true;
+    sym = 0;
+    return 1;
+  }
+  sym = __ldg(T.sorted + ((w >> (32 - L)) + T.base[L]));
+  return L;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// Exclusive block scan of per-thread counts; returns the exclusive prefix and
+// writes the block total to *total.  Uses s_warp[B/32]; ends with a barrier.
+template <int B>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t c, uint32_t* s_warp,
+                                                    uint32_t* total) {
+  constexpr int NW = B / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t incl = warp_incl_scan(c, lane);
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = lane < NW ? s_warp[lane] : 0u;
+    v = warp_incl_scan(v, lane);
+    if (lane < NW) s_warp[lane] = v;
+  }
+  __syncthreads();
+  *total = s_warp[NW - 1];
+  return (warp ? s_warp[warp - 1] : 0u) + incl - c;
+}
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Waits a little; returns false once the launch was aborted or the wait
+// started at t0 exceeded the limit (the caller records a timeout and stops
+// waiting).
+__device__ __forceinline__ bool backoff_wait(const DecodeParams& P, uint64_t t0) {
+  if (ld_relaxed32(P.abort_flag)) return false;
+  if (now_ns() - t0 > P.timeout_ns) {
+    atomicExch(P.abort_flag, 1u);
+    return false;
+  }
+  __nanosleep(64);
+  return true;
+}
+
+// Decoupled look-back over the work units of one field (warp 0 only).
+// Publishes this unit's count as an aggregate, sums predecessors' aggregates
+// back to the nearest inclusive prefix, then publishes its own inclusive
+// prefix.  Returns the exclusive prefix (the unit's first output index).
+__device__ __forceinline__ uint64_t lookback_counts(const DecodeParams& P, uint64_t g,
+                                                    uint64_t first_unit, uint64_t C,
+                                                    uint32_t* err) {
+  const int lane = threadIdx.x & 31;
+  uint64_t* st = P.unit_state;
+  if (g == first_unit) {
+    if (lane == 0) st_relaxed(st + g, kStateInc | C);
+    return 0;
+  }
+  if (lane == 0) st_relaxed(st + g, kStateAgg | C);
+  uint64_t excl = 0;
+  int64_t j = static_cast<int64_t>(g) - 1;
+  const int64_t lo = static_cast<int64_t>(first_unit);
+  const uint64_t t0 = now_ns();
+  for (;;) {
+    const int64_t idx = j - lane;
+    const uint64_t s = idx >= lo ? ld_relaxed(st + idx) : kStateInc;
+    const uint32_t flag = static_cast<uint32_t>(s >> 62);
+    const uint32_t inc = __ballot_sync(0xffffffffu, flag == 2u);
+    const uint32_t notready = __ballot_sync(0xffffffffu, flag == 0u);
+    const uint32_t need = inc ? (((inc & (0u - inc)) << 1) - 1u) : 0xffffffffu;
+    if (notready & need) {
+      bool go = true;
+      if (lane == 0) go = backoff_wait(P, t0);
+      go = __shfl_sync(0xffffffffu, go, 0);
+      if (!go) {
+        if (lane == 0) atomicOr(err, kErrTimeout);
+        break;
+      }
+      continue;
+    }
+    excl += warp_sum_u64((need >> lane) & 1u ? (s & kStateValMask) : 0ull);
+    if (inc) break;
+    j -= 32;
+  }
+  if (lane == 0) st_relaxed(st + g, kStateInc | ((excl + C) & kStateValMask));
+  return excl;
+}
+
+// Algorithm 1 (Sec. IV-B): the block's output [0, C) is produced through a
+// shared-memory window of `window` symbols.  A thread decodes its whole range
+// [o, o + c) into the window only when it fits; the first thread that does
+// not fit ends the window, the window is written to global memory with
+// coalesced 16-byte stores, and the next window starts at that thread.
+// `decode(dst)` writes the thread's c symbols to dst[0 .. c).
+// Requires window >= max c (c <= S).  Global writes are clipped to [0, n).
+template <int B, class DecodeFn>
+__device__ __forceinline__ void window_write(uint16_t* s_out, uint32_t* s_flush_end,
+                                             uint32_t window, uint32_t o, uint32_t c,
+                                             uint32_t C, uint64_t base, uint16_t* out,
+                                             uint64_t n, DecodeFn&& decode) {
+  const int t = threadIdx.x;
+  const uint32_t off0 = static_cast<uint32_t>((reinterpret_cast<uintptr_t>(out) >> 1) & 7u);
+  // out - off0 is 16-byte aligned; virtual index X = x + off0
+  uint16_t* out_al = out - off0;
+  bool done = c == 0;
+  uint32_t ws = 0;
+  while (ws < C) {
+    const uint32_t we = ws + window;
+    if (t == 0) *s_flush_end = C < we ? C : we;
+    __syncthreads();
+    if (!done && o < we && o + c > we) atomicMin(s_flush_end, o);
+    __syncthreads();
+    const uint32_t fe = *s_flush_end;
+    const uint64_t X0 = base + ws + off0;
+    const uint32_t pad = static_cast<uint32_t>(X0 & 7u);
+    if (!done && o + c <= fe) {
+      decode(s_out + pad + (o - ws));
+      done = true;
+    }
+    __syncthreads();
+    // store virtual range [X0, Xe) from s_out[X - a0]
+    const uint64_t a0 = X0 & ~7ull;
+    const uint64_t Xe = base + fe + off0;
+    const uint64_t Xn = n + off0;  // first virtual index past the output
+    const uint64_t q0 = a0 >> 3, q1 = (Xe + 7) >> 3;
+    for (uint64_t q = q0 + t; q < q1; q += B) {
+      const uint64_t Xq = q << 3;
+      if (Xq >= X0 && Xq + 8 <= Xe && Xq + 8 <= Xn) {
+        *reinterpret_cast<uint4*>(out_al + Xq) =
+            *reinterpret_cast<const uint4*>(s_out + (Xq - a0));
+      } else {
+        const uint64_t lo = Xq > X0 ? Xq : X0;
+        uint64_t hi = Xq + 8 < Xe ? Xq + 8 : Xe;
+        hi = hi < Xn ? hi : Xn;
+        for (uint64_t X = lo; X < hi; ++X) out_al[X] = s_out[X - a0];
+      }
+    }
+    __syncthreads();
+    ws = fe;
+  }
+}
+
+// Loads the decode table of a field into shared memory (whole block).
+__device__ __forceinline__ void load_table(const TableHeader* H, uint32_t K, uint32_t* s_lut,
+                                           uint64_t* s_end, uint32_t* s_base,
+                                           uint32_t* s_meta, int nthreads) {
+  const int t = threadIdx.x;
+  const uint4* src =
+      reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(H) + kTableHeaderBytes);
+  uint4* dst = reinterpret_cast<uint4*>(s_lut);
+  const uint32_t nv = (1u << K) / 4;
+  for (uint32_t k = t; k < nv; k += nthreads) dst[k] = __ldg(src + k);
+  if (t < 34) {
+    s_end[t] = H->end[t];
+    s_base[t] = H->base[t];
+  }
+  if (t == 0) {
+    s_meta[0] = H->maxlen;
+    s_meta[1] = H->status;
+  }
+}
+
+__device__ __forceinline__ const FieldDesc& field_of(const DecodeParams& P, uint32_t f) {
+  return P.nfields == 1 ? P.f0 : P.fields[f];
+}
+
+// Index of the field whose work units contain unit g (fields are in order).
+__device__ __forceinline__ uint32_t find_field(const DecodeParams& P, uint64_t g) {
+  if (P.nfields == 1) return 0;
+  uint32_t lo = 0, hi = P.nfields - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (P.fields[mid].unit_begin <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Copies subsequence i (S bits, plus the following unit that a codeword
+// starting near its end may reach) into a shared-memory column with stride
+// `stride`.  Units past the readable stream read as zero.
+template <int S>
+__device__ __forceinline__ void stage_units(uint32_t* col, const FieldDesc& F, uint64_t i,
+                                            int stride) {
+  constexpr int U = S / 32;
+  const uint64_t w0 = i * U;
+  const uint32_t* src = F.words + w0;
+  if (w0 + U <= F.nwords) {
+    if constexpr (U == 2) {
+      const uint2 v = ldg_v2(src);
+      col[0] = v.x;
+      col[stride] = v.y;
+    } else {
+#pragma unroll
+      for (int h = 0; h < U / 4; ++h) {
+        const uint4 v = ldg_v4(src + 4 * h);
+        col[(4 * h + 0) * stride] = v.x;
+        col[(4 * h + 1) * stride] = v.y;
+        col[(4 * h + 2) * stride] = v.z;
+        col[(4 * h + 3) * stride] = v.w;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < U; ++k) col[k * stride] = (w0 + k < F.nwords) ? __ldg(src + k) : 0u;
+  }
+  col[U * stride] = (w0 + U < F.nwords) ? __ldg(src + U) : 0u;
+}
+
+}  // namespace dev
+}  // namespace hd

@@ -1,0 +1,38 @@
+// kernels.h -- host-side launchers of the decode kernels (C++ linkage, used
+// by the C-ABI layer).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace hd {
+
+// Builds every field's decode table and clears the per-launch control region.
+cudaError_t launch_prepare(const PrepParams& p, cudaStream_t stream);
+
+// Bytes of a decode table with K index bits for an alphabet (256-byte multiple).
+size_t table_bytes(uint32_t K, uint32_t alphabet);
+
+struct LaunchShape {
+  uint32_t S;        // decoder subsequence bits
+  uint32_t threads;  // threads per block = subsequences per tile
+  uint32_t window;   // output window (symbols)
+  uint32_t K;        // table bits
+  uint32_t M;        // tiles per work unit (look-back granularity)
+  uint32_t grid;     // persistent blocks (0: full occupancy)
+};
+
+// Dynamic shared memory one decode block needs for a launch shape.
+size_t decode_smem_bytes(const LaunchShape& s, bool self_sync);
+
+// Decodes all fields of `p` with the gap-array variant (Sec. III-C) or the
+// self-synchronising variant (Sec. III-B, IV-A); with p.sync_only the latter
+// writes the gap arrays instead of decoding.
+cudaError_t launch_decode(const DecodeParams& p, const LaunchShape& s, bool self_sync,
+                          int num_sms, cudaStream_t stream);
+
+}  // namespace hd

@@ -1,0 +1,168 @@
+// table.cu -- builds the shared-memory decode table of each field's canonical
+// codebook on the GPU and clears the per-launch look-back state.
+//
+// The paper keeps the codebook in global memory and relies on the cache
+// (Sec. IV-B); here every decode block copies a direct-lookup table into shared
+// memory instead, so a codeword is resolved with one shared-memory load.  The
+// table is derived from the code lengths alone because the codes are canonical
+// (RFC 1951 Sec. 3.2.2 assignment).
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace hd {
+
+namespace {
+
+constexpr int kPrepThreads = 1024;
+
+__device__ __forceinline__ const FieldDesc& field_at(const PrepParams& p, uint32_t i) {
+  return p.nfields == 1 ? p.f0 : p.fields[i];
+}
+
+// One block builds the table of one field.
+__device__ void build_table(const FieldDesc& F, uint32_t K) {
+  __shared__ uint32_t cnt[34];
+  __shared__ uint32_t s_maxlen, s_bad, s_nused;
+  __shared__ uint64_t s_end[34];
+  __shared__ uint32_t s_start[34];
+  __shared__ uint32_t s_base[34];
+  __shared__ uint32_t wcnt[kPrepThreads / 32][34];
+  __shared__ uint32_t run[34];
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const uint32_t A = F.alphabet;
+  TableHeader* H = const_cast<TableHeader*>(F.table);
+  uint32_t* lut = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(H) + kTableHeaderBytes);
+  uint16_t* sorted = reinterpret_cast<uint16_t*>(lut + (1u << K));
+
+  if (t < 34) {
+    cnt[t] = 0;
+    run[t] = 0;
+  }
+  if (t == 0) {
+    s_maxlen = 0;
+    s_bad = 0;
+    s_nused = 0;
+  }
+  __syncthreads();
+  for (uint32_t s = t; s < A; s += kPrepThreads) {
+    const uint32_t L = F.lengths[s];
+    if (L > kMaxCodeLen) {
+      atomicOr(&s_bad, 1u);
+    } else if (L) {
+      atomicAdd(&cnt[L], 1u);
+      atomicMax(&s_maxlen, L);
+      atomicAdd(&s_nused, 1u);
+    }
+  }
+  __syncthreads();
+  if (t == 0) {
+    // Kraft sum in units of 2^-32 must not exceed 1
+    uint64_t kraft = 0;
+    for (int L = 1; L <= 32; ++L) kraft += static_cast<uint64_t>(cnt[L]) << (32 - L);
+    if (kraft > (1ull << 32)) s_bad = 1;
+    uint64_t code = 0;
+    uint32_t start = 0;
+    s_end[0] = 0;
+    s_start[0] = 0;
+    s_base[0] = 0;
+    for (int L = 1; L <= 33; ++L) {
+      const uint64_t c_prev = (L >= 2) ? cnt[L - 1] : 0;
+      if (L <= 32) {
+        code = (code + c_prev) << 1;  // first canonical code of length L
+        s_start[L] = start;
+        s_base[L] = start - static_cast<uint32_t>(code);
+        s_end[L] = (code + cnt[L]) << (32 - L);
+        start += cnt[L];
+      } else {
+        s_start[L] = start;
+        s_base[L] = 0;
+        s_end[L] = s_end[32];
+      }
+    }
+    H->status = s_bad;
+    H->maxlen = s_maxlen;
+    H->nused = s_nused;
+    H->K = K;
+    for (int L = 0; L < 34; ++L) {
+      H->end[L] = s_end[L];
+      H->base[L] = s_base[L];
+    }
+  }
+  __syncthreads();
+  if (s_bad) return;
+
+  // Rank of each symbol among the symbols of its length, in symbol order:
+  // within a warp via match/popc, across warps via per-length counters.
+  for (uint32_t c0 = 0; c0 < A; c0 += kPrepThreads) {
+    for (int k = t; k < (kPrepThreads / 32) * 34; k += kPrepThreads) (&wcnt[0][0])[k] = 0;
+    __syncthreads();
+    const uint32_t s = c0 + t;
+    const uint32_t L = s < A ? F.lengths[s] : 0u;
+    const uint32_t same = __match_any_sync(0xffffffffu, L);
+    const uint32_t rank_w = __popc(same & ((1u << lane) - 1u));
+    if (L && rank_w == 0) wcnt[warp][L] = __popc(same);
+    __syncthreads();
+    if (t >= 1 && t <= 32) {
+      uint32_t acc = run[t];
+      for (int w = 0; w < kPrepThreads / 32; ++w) {
+        const uint32_t v = wcnt[w][t];
+        wcnt[w][t] = acc;
+        acc += v;
+      }
+      run[t] = acc;
+    }
+    __syncthreads();
+    if (L) sorted[s_start[L] + wcnt[warp][L] + rank_w] = static_cast<uint16_t>(s);
+    __syncthreads();
+  }
+
+  // First-level table: entry p covers all windows whose top K bits equal p.
+  const uint32_t maxlen = s_maxlen;
+  for (uint32_t p = t; p < (1u << K); p += kPrepThreads) {
+    const uint32_t w = p << (32 - K);
+    uint32_t L = 1;
+    while (L <= 32 && static_cast<uint64_t>(w) >= s_end[L]) ++L;
+    uint32_t e;
+    if (L <= K && L <= maxlen) {
+      const uint32_t rank = (w >> (32 - L)) + s_base[L];
+      e = (L << 16) | sorted[rank];
+    } else {
+      e = kLongFlag | (L <= maxlen ? L : 33u);
+    }
+    lut[p] = e;
+  }
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_prepare(const __grid_constant__ PrepParams P) {
+  const uint32_t b = blockIdx.x;
+  if (b < P.nfields) {
+    build_table(field_at(P, b), P.K);
+    return;
+  }
+  // clear the per-launch control region (tickets, error words, look-back states)
+  const uint64_t zb = b - P.nfields;
+  const uint4 z = make_uint4(0, 0, 0, 0);
+  for (uint64_t i = zb * kPrepThreads + threadIdx.x; i < P.zero_vec;
+       i += static_cast<uint64_t>(P.zero_blocks) * kPrepThreads)
+    P.zero_ptr[i] = z;
+}
+
+}  // namespace
+
+cudaError_t launch_prepare(const PrepParams& p, cudaStream_t stream) {
+  const uint32_t zb = p.zero_blocks;
+  const uint32_t grid = p.nfields + zb;
+  if (grid == 0) return cudaSuccess;
+  k_prepare<<<grid, kPrepThreads, 0, stream>>>(p);
+  return cudaGetLastError();
+}
+
+size_t table_bytes(uint32_t K, uint32_t alphabet) {
+  size_t b = kTableHeaderBytes + (static_cast<size_t>(1) << K) * 4 + static_cast<size_t>(alphabet) * 2;
+  return (b + 255) & ~static_cast<size_t>(255);
+}
+
+}  // namespace hd

@@ -1,0 +1,303 @@
+"""Thin ctypes binding of libhd.so (include/hd.h).
+
+Argument marshalling only: every step of the decode path runs in the library's
+CUDA kernels.  Device buffers and streams come from PyTorch.  If the library
+cannot be loaded the import of any function here raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+HD_OK = 0
+HD_PENDING = 1
+HD_ERR_ARG = -1
+HD_ERR_CAPACITY = -2
+HD_ERR_SYMBOL = -3
+HD_ERR_CORRUPT = -4
+HD_ERR_NOSYNC = -5
+HD_ERR_TIMEOUT = -6
+HD_ERR_CUDA = -7
+HD_ERR_NOMEM = -8
+HD_ERR_BUSY = -9
+
+_NAMES = {
+    0: "HD_OK", 1: "HD_PENDING", -1: "HD_ERR_ARG", -2: "HD_ERR_CAPACITY", -3: "HD_ERR_SYMBOL",
+    -4: "HD_ERR_CORRUPT", -5: "HD_ERR_NOSYNC", -6: "HD_ERR_TIMEOUT", -7: "HD_ERR_CUDA",
+    -8: "HD_ERR_NOMEM", -9: "HD_ERR_BUSY",
+}
+
+
+class HDError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__(f"{fn} returned {_NAMES.get(code, code)}")
+        self.code = code
+
+
+class hd_stream_info(ctypes.Structure):
+    _fields_ = [("nbits", ctypes.c_uint64), ("nwords", ctypes.c_uint64),
+                ("nsub", ctypes.c_uint64)]
+
+
+class hd_field(ctypes.Structure):
+    _fields_ = [("words", ctypes.c_void_p), ("nwords", ctypes.c_uint64),
+                ("nbits", ctypes.c_uint64), ("gap", ctypes.c_void_p),
+                ("subseq_bits", ctypes.c_uint32), ("lengths", ctypes.c_void_p),
+                ("alphabet", ctypes.c_uint32), ("n", ctypes.c_uint64)]
+
+
+class hd_config(ctypes.Structure):
+    _fields_ = [("subseq_bits", ctypes.c_uint32), ("threads", ctypes.c_uint32),
+                ("window", ctypes.c_uint32), ("lut_bits", ctypes.c_uint32),
+                ("tiles_per_unit", ctypes.c_uint32)]
+
+
+# every exported symbol of include/hd.h with its ctypes signature
+_P = ctypes.c_void_p
+_SIGS = {
+    "hd_build_codebook": ([_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _P],
+                          ctypes.c_int),
+    "hd_encode": ([_P, ctypes.c_uint64, _P, ctypes.c_uint32, ctypes.c_uint32, _P,
+                   ctypes.c_uint64, _P, ctypes.c_uint64, ctypes.POINTER(hd_stream_info)],
+                  ctypes.c_int),
+    "hd_ctx_create": ([ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
+    "hd_ctx_destroy": ([_P], ctypes.c_int),
+    "hd_set_config": ([_P, ctypes.POINTER(hd_config)], ctypes.c_int),
+    "hd_get_config": ([_P, ctypes.POINTER(hd_config)], ctypes.c_int),
+    "hd_decode": ([_P, ctypes.POINTER(hd_field), _P, _P], ctypes.c_int),
+    "hd_status": ([_P, _P], ctypes.c_int),
+    "hd_sync_points": ([_P, ctypes.POINTER(hd_field), _P, _P], ctypes.c_int),
+    "hd_decode_batch": ([_P, ctypes.POINTER(hd_field), ctypes.c_uint32, _P, _P], ctypes.c_int),
+    "hd_batch_status": ([_P, _P, ctypes.c_uint32, _P], ctypes.c_int),
+    "hd_decode_host": ([_P, ctypes.POINTER(hd_field), _P, _P], ctypes.c_int),
+    "hd_profile": ([_P, ctypes.c_int], ctypes.c_int),
+    "hd_kernel_time": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
+                       ctypes.c_int),
+    "hd_launch_count": ([_P], ctypes.c_uint64),
+    "hd_version": ([], ctypes.c_char_p),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Loads libhd.so (building it first when sources changed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_needed else _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libhd.so not found at {path}; run paper_2201_09118_gb300.build")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _check(fn: str, rc: int):
+    if rc != HD_OK:
+        raise HDError(fn, rc)
+    return rc
+
+
+def _np_ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    h = getattr(stream, "cuda_stream", stream)
+    return ctypes.c_void_p(int(h) if h else 0)
+
+
+# ---------------------------------------------------------------------------
+# host-side codebook / encoder
+# ---------------------------------------------------------------------------
+
+
+def hd_build_codebook(codes: np.ndarray, alphabet: int, max_len: int = 32) -> np.ndarray:
+    codes = np.ascontiguousarray(codes, dtype=np.uint16)
+    out = np.zeros(alphabet, dtype=np.uint8)
+    _check("hd_build_codebook",
+           load().hd_build_codebook(_np_ptr(codes), codes.size, alphabet, max_len, _np_ptr(out)))
+    return out
+
+
+def hd_encode(codes: np.ndarray, lengths: np.ndarray, subseq_bits: int = 128,
+              with_gap: bool = True) -> dict:
+    """Returns {'words', 'gap' (or None), 'nbits', 'nwords', 'nsub'}."""
+    codes = np.ascontiguousarray(codes, dtype=np.uint16)
+    lengths = np.ascontiguousarray(lengths, dtype=np.uint8)
+    lib = load()
+    info = hd_stream_info()
+    rc = lib.hd_encode(_np_ptr(codes), codes.size, _np_ptr(lengths), lengths.size, subseq_bits,
+                       None, 0, None, 0, ctypes.byref(info))
+    if rc not in (HD_OK, HD_ERR_CAPACITY):
+        raise HDError("hd_encode", rc)
+    words = np.zeros(max(1, info.nwords), dtype=np.uint32)
+    gap = np.zeros(max(1, info.nsub), dtype=np.uint8) if with_gap else None
+    _check("hd_encode", lib.hd_encode(_np_ptr(codes), codes.size, _np_ptr(lengths), lengths.size,
+                                      subseq_bits, _np_ptr(words), words.size,
+                                      _np_ptr(gap) if gap is not None else None,
+                                      gap.size if gap is not None else 0, ctypes.byref(info)))
+    return {"words": words[:info.nwords], "gap": None if gap is None else gap[:info.nsub],
+            "nbits": int(info.nbits), "nwords": int(info.nwords), "nsub": int(info.nsub),
+            "subseq_bits": subseq_bits}
+
+
+# ---------------------------------------------------------------------------
+# device fields and context
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class DeviceField:
+    """An encoded field resident on the GPU (torch tensors own the memory)."""
+    words: "object"            # torch.int32 tensor (the uint32 units)
+    nbits: int
+    gap: Optional["object"]    # torch.uint8 tensor or None
+    subseq_bits: int
+    lengths: "object"          # torch.uint8 tensor [alphabet]
+    alphabet: int
+    n: int
+
+    def c_struct(self) -> hd_field:
+        return hd_field(self.words.data_ptr(), self.words.numel(), self.nbits,
+                        self.gap.data_ptr() if self.gap is not None else None,
+                        self.subseq_bits, self.lengths.data_ptr(), self.alphabet, self.n)
+
+    @staticmethod
+    def upload(enc: dict, lengths: np.ndarray, n: int, device="cuda", with_gap: bool = True):
+        import torch
+        words = torch.from_numpy(enc["words"].view(np.int32).copy()).to(device)
+        gap = None
+        if with_gap and enc.get("gap") is not None:
+            g = enc["gap"] if enc["gap"].size else np.zeros(1, np.uint8)
+            gap = torch.from_numpy(np.ascontiguousarray(g)).to(device)
+        lt = torch.from_numpy(np.ascontiguousarray(lengths, dtype=np.uint8)).to(device)
+        return DeviceField(words, int(enc["nbits"]), gap, int(enc["subseq_bits"]), lt,
+                           int(lengths.size), int(n))
+
+
+class Context:
+    """Owns an hd_ctx for one device."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        _check("hd_ctx_create", self._lib.hd_ctx_create(device, ctypes.byref(h)))
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            self._lib.hd_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_config(self, subseq_bits=0, threads=0, window=0, lut_bits=0, tiles_per_unit=0):
+        cfg = hd_config(subseq_bits, threads, window, lut_bits, tiles_per_unit)
+        _check("hd_set_config", self._lib.hd_set_config(self.handle, ctypes.byref(cfg)))
+
+    def reset_config(self):
+        _check("hd_set_config", self._lib.hd_set_config(self.handle, None))
+
+    def get_config(self) -> dict:
+        cfg = hd_config()
+        _check("hd_get_config", self._lib.hd_get_config(self.handle, ctypes.byref(cfg)))
+        return {"subseq_bits": cfg.subseq_bits, "threads": cfg.threads, "window": cfg.window,
+                "lut_bits": cfg.lut_bits, "tiles_per_unit": cfg.tiles_per_unit}
+
+    def decode(self, field: DeviceField, out, stream=None) -> None:
+        f = field.c_struct()
+        _check("hd_decode", self._lib.hd_decode(self.handle, ctypes.byref(f),
+                                                 ctypes.c_void_p(out.data_ptr()),
+                                                 _stream_handle(stream)))
+
+    def status(self, stream=None) -> int:
+        return self._lib.hd_status(self.handle, _stream_handle(stream))
+
+    def sync_points(self, field: DeviceField, gap_out, stream=None) -> None:
+        f = field.c_struct()
+        _check("hd_sync_points", self._lib.hd_sync_points(self.handle, ctypes.byref(f),
+                                                           ctypes.c_void_p(gap_out.data_ptr()),
+                                                           _stream_handle(stream)))
+
+    def decode_batch(self, fields: Sequence[DeviceField], outs, stream=None) -> None:
+        nf = len(fields)
+        arr = (hd_field * max(1, nf))(*[f.c_struct() for f in fields])
+        ptrs = (ctypes.c_void_p * max(1, nf))(*[o.data_ptr() for o in outs])
+        _check("hd_decode_batch", self._lib.hd_decode_batch(self.handle, arr, nf, ptrs,
+                                                             _stream_handle(stream)))
+
+    def batch_status(self, nf: int, stream=None):
+        st = np.zeros(max(1, nf), dtype=np.int32)
+        rc = self._lib.hd_batch_status(self.handle, _np_ptr(st), nf, _stream_handle(stream))
+        return rc, st[:nf]
+
+    def decode_host(self, enc: dict, lengths: np.ndarray, n: int, out: np.ndarray = None,
+                    stream=None, with_gap: bool = True) -> np.ndarray:
+        """Host buffers in, host symbols out (copies inside the call)."""
+        words = np.ascontiguousarray(enc["words"], dtype=np.uint32)
+        gap = enc.get("gap") if with_gap else None
+        if gap is not None:
+            gap = np.ascontiguousarray(gap, dtype=np.uint8)
+        lengths = np.ascontiguousarray(lengths, dtype=np.uint8)
+        if out is None:
+            out = np.empty(max(1, n), dtype=np.uint16)
+        f = hd_field(words.ctypes.data, words.size, int(enc["nbits"]),
+                     gap.ctypes.data if gap is not None and gap.size else None,
+                     int(enc["subseq_bits"]), lengths.ctypes.data, lengths.size, n)
+        _check("hd_decode_host", self._lib.hd_decode_host(self.handle, ctypes.byref(f),
+                                                          _np_ptr(out), _stream_handle(stream)))
+        return out[:n]
+
+    def decode_host_ptrs(self, words_ptr: int, nwords: int, nbits: int, gap_ptr: int,
+                         subseq_bits: int, lengths_ptr: int, alphabet: int, n: int,
+                         out_ptr: int, stream=None) -> int:
+        """Raw-pointer variant (e.g. pinned torch tensors); returns the status."""
+        f = hd_field(words_ptr, nwords, nbits, gap_ptr or None, subseq_bits, lengths_ptr,
+                     alphabet, n)
+        return self._lib.hd_decode_host(self.handle, ctypes.byref(f), ctypes.c_void_p(out_ptr),
+                                        _stream_handle(stream))
+
+    def profile(self, enable: bool = True):
+        _check("hd_profile", self._lib.hd_profile(self.handle, 1 if enable else 0))
+
+    def kernel_time(self):
+        ms = ctypes.c_double()
+        n = ctypes.c_uint64()
+        _check("hd_kernel_time", self._lib.hd_kernel_time(self.handle, ctypes.byref(ms),
+                                                          ctypes.byref(n)))
+        return ms.value, n.value
+
+    def launch_count(self) -> int:
+        return int(self._lib.hd_launch_count(self.handle))
+
+
+def hd_version() -> str:
+    return load().hd_version().decode()

@@ -1,0 +1,299 @@
+"""GPU parity: the CUDA decoder (through the C ABI) against the CPU oracle.
+
+Every stream decoded here is produced by the oracle's encoder and every
+expected value is the oracle's decode (which the pins in test_oracle.py tie to
+the paper).  Decoding is integer work, so parity is bit-exact.
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+CANARY = 0xABCD
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_09118_gb300 import hd
+    c = hd.Context(0)
+    yield c
+    c.close()
+
+
+def dev_field(c, with_gap=True):
+    from paper_2201_09118_gb300 import hd
+    enc = {"words": c["words"], "gap": c["gap"], "nbits": c["nbits"], "subseq_bits": c["S"]}
+    return hd.DeviceField.upload(enc, c["lengths"], c["n"], with_gap=with_gap)
+
+
+def run_decode(ctx, c, with_gap=True, stream=None):
+    f = dev_field(c, with_gap)
+    out = torch.full((c["n"] + 64,), CANARY, dtype=torch.int32).to(torch.int16).cuda()
+    ctx.decode(f, out, stream)
+    st = ctx.status(stream)
+    res = out.cpu().numpy().view(np.uint16)
+    return st, res
+
+
+def expect(c):
+    return oracle.decode(c["words"], c["nbits"], c["codes"], c["lengths"], n_cap=max(1, c["n"]))
+
+
+def check(ctx, c, with_gap=True):
+    from paper_2201_09118_gb300 import hd
+    st, res = run_decode(ctx, c, with_gap)
+    assert st == hd.HD_OK
+    ref = expect(c)
+    assert ref.size == c["n"]
+    got = res[:c["n"]]
+    if not np.array_equal(got, ref):
+        bad = np.nonzero(got != ref)[0]
+        raise AssertionError(f"{bad.size} mismatches, first at {bad[:8].tolist()}")
+    assert np.all(res[c["n"]:] == np.uint16(CANARY)), "write past the output"
+
+
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("with_gap", [True, False], ids=["gap", "selfsync"])
+def test_laplace_2pow20(ctx, with_gap):
+    x = synth.laplace_codes(1 << 20, scale=2.0, seed=1000)
+    c = oracle.compress(x, 1024, S=128)
+    check(ctx, c, with_gap)
+
+
+def test_sync_points_equal_gap_array(ctx):
+    x = synth.laplace_codes(300001, scale=20.0, seed=77)
+    for S in (64, 128, 256):
+        c = oracle.compress(x, 1024, S=S)
+        f = dev_field(c, with_gap=False)
+        nsub = c["gap"].size
+        gout = torch.full((nsub + 16,), 255, dtype=torch.uint8, device="cuda")
+        ctx.sync_points(f, gout)
+        assert ctx.status() == 0
+        got = gout.cpu().numpy()
+        sync, _ = oracle.sync_points(c["words"], c["nbits"], c["codes"], c["lengths"], S)
+        ref = (sync - np.arange(nsub, dtype=np.uint64) * S).astype(np.uint8)
+        assert np.array_equal(got[:nsub], ref)
+        assert np.array_equal(got[:nsub], c["gap"])
+        assert np.all(got[nsub:] == 255)
+
+
+@pytest.mark.parametrize("S", [64, 128, 256])
+@pytest.mark.parametrize("threads", [128, 256, 512])
+@pytest.mark.parametrize("with_gap", [True, False], ids=["gap", "selfsync"])
+def test_launch_shapes(ctx, S, threads, with_gap):
+    x = synth.laplace_codes(200003, scale=30.0, seed=S + threads)
+    c = oracle.compress(x, 1024, S=S)
+    try:
+        for window, K, M in ((S, 8, 1), (1024, 11, 2), (4096, 12, 8), (8192, 13, 16)):
+            ctx.set_config(subseq_bits=S, threads=threads, window=max(window, S), lut_bits=K,
+                           tiles_per_unit=M)
+            check(ctx, c, with_gap)
+    finally:
+        ctx.reset_config()
+
+
+@pytest.mark.parametrize("dec_S", [128, 256])
+def test_decoder_subsequence_multiple_of_stream(ctx, dec_S):
+    x = synth.laplace_codes(100000, scale=3.0, seed=5)
+    c = oracle.compress(x, 1024, S=64)
+    try:
+        ctx.set_config(subseq_bits=dec_S)
+        check(ctx, c, True)
+    finally:
+        ctx.reset_config()
+
+
+@pytest.mark.parametrize("with_gap", [True, False], ids=["gap", "selfsync"])
+@pytest.mark.parametrize("case", ["n1", "n2", "n3", "one_symbol", "two_symbols_skew",
+                                  "fibonacci32", "alphabet256", "alphabet4096", "skew1e-2",
+                                  "uniform_equal_lengths", "ragged"])
+def test_edge_cases(ctx, case, with_gap):
+    rng = np.random.default_rng(zlib.crc32(case.encode()))
+    A = 1024
+    if case == "n1":
+        x = np.array([517], np.uint16)
+    elif case == "n2":
+        x = np.array([3, 900], np.uint16)
+    elif case == "n3":
+        x = np.array([3, 900, 3], np.uint16)
+    elif case == "one_symbol":
+        x = np.full(300000, 512, np.uint16)
+    elif case == "two_symbols_skew":
+        x = np.where(rng.random(200000) < 0.999, 512, 7).astype(np.uint16)
+    elif case == "fibonacci32":
+        # Fibonacci histogram F1..F34: Huffman depth 33, limited to 32 bits
+        fib = [1, 1]
+        while len(fib) < 34:
+            fib.append(fib[-1] + fib[-2])
+        x = rng.permutation(np.repeat(np.arange(34, dtype=np.uint16), fib))
+        A = 64
+    elif case == "alphabet256":
+        x = synth.smooth_codes_1d(150000, 1e-5, alphabet=256, seed=8)
+        A = 256
+    elif case == "alphabet4096":
+        x = synth.smooth_codes_1d(150000, 1e-6, alphabet=4096, seed=9)
+        A = 4096
+    elif case == "skew1e-2":
+        x = synth.smooth_codes_1d(400000, 1e-2, seed=10)
+    elif case == "uniform_equal_lengths":
+        x = (np.arange(70000) % 8).astype(np.uint16)
+        A = 8
+    else:  # ragged
+        x = synth.laplace_codes(777777, scale=7.0, seed=11)
+    c = oracle.compress(x, A, S=128)
+    if case == "fibonacci32":
+        assert int(c["lengths"].max()) == 32
+    check(ctx, c, with_gap)
+
+
+def test_decode_host(ctx):
+    from paper_2201_09118_gb300 import hd
+    x = synth.laplace_codes(500000, scale=4.0, seed=12)
+    c = oracle.compress(x, 1024, S=128)
+    enc = {"words": c["words"], "gap": c["gap"], "nbits": c["nbits"], "subseq_bits": 128}
+    got = ctx.decode_host(enc, c["lengths"], c["n"])
+    assert np.array_equal(got, expect(c))
+    got2 = ctx.decode_host(enc, c["lengths"], c["n"], with_gap=False)
+    assert np.array_equal(got2, expect(c))
+    assert hd.HD_OK == 0
+
+
+def test_batch_mixed_fields(ctx):
+    from paper_2201_09118_gb300 import hd
+    specs = synth.batch_spec(12, lo=1 << 10, hi=1 << 18, seed=55)
+    comps, fields, outs = [], [], []
+    for sp in specs:
+        x = synth.smooth_codes_1d(sp.n, sp.rel_eb, alphabet=sp.alphabet, seed=sp.seed)
+        c = oracle.compress(x, sp.alphabet, S=128)
+        comps.append(c)
+        fields.append(dev_field(c, True))
+        outs.append(torch.full((c["n"] + 16,), CANARY, dtype=torch.int32).to(torch.int16).cuda())
+    ctx.decode_batch(fields, outs)
+    rc, st = ctx.batch_status(len(fields))
+    assert rc == hd.HD_OK and np.all(st == 0)
+    for c, o in zip(comps, outs):
+        r = o.cpu().numpy().view(np.uint16)
+        assert np.array_equal(r[:c["n"]], expect(c))
+        assert np.all(r[c["n"]:] == np.uint16(CANARY))
+
+
+# ---------------------------------------------------------------------------
+# corrupt and invalid inputs: error codes, no hang, nothing written past n
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("with_gap", [True, False], ids=["gap", "selfsync"])
+def test_corrupt_streams(ctx, with_gap):
+    from paper_2201_09118_gb300 import hd
+    x = synth.laplace_codes(200000, scale=6.0, seed=13)
+    c = oracle.compress(x, 1024, S=128)
+    # claimed symbol count differs from the stream
+    for dn in (-1, 1):
+        cc = dict(c)
+        cc["n"] = c["n"] + dn
+        st, res = run_decode(ctx, cc, with_gap)
+        assert st == hd.HD_ERR_CORRUPT
+        assert np.all(res[cc["n"]:] == np.uint16(CANARY))
+    # truncated stream
+    cc = dict(c)
+    cc["nbits"] = c["nbits"] - 5
+    st, res = run_decode(ctx, cc, with_gap)
+    assert st == hd.HD_ERR_CORRUPT
+    assert np.all(res[cc["n"]:] == np.uint16(CANARY))
+    # flipped bits: either still a valid stream of n symbols or detected
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        cc = dict(c)
+        w = c["words"].copy()
+        b = int(rng.integers(0, c["nbits"]))
+        w[b >> 5] ^= np.uint32(1 << (31 - (b & 31)))
+        cc["words"] = w
+        st, res = run_decode(ctx, cc, with_gap)
+        assert st in (hd.HD_OK, hd.HD_ERR_CORRUPT)
+        assert np.all(res[cc["n"]:] == np.uint16(CANARY))
+    if with_gap:
+        cc = dict(c)
+        g = c["gap"].copy()
+        g[len(g) // 2] = 200
+        cc["gap"] = g
+        st, res = run_decode(ctx, cc, True)
+        assert st == hd.HD_ERR_CORRUPT
+        g = c["gap"].copy()
+        g[len(g) // 3] ^= 1
+        cc["gap"] = g
+        st, res = run_decode(ctx, cc, True)
+        assert st == hd.HD_ERR_CORRUPT
+
+
+def test_invalid_codebook_and_arguments(ctx):
+    from paper_2201_09118_gb300 import hd
+    x = synth.laplace_codes(10000, seed=14)
+    c = oracle.compress(x, 1024, S=128)
+    cc = dict(c)
+    L = c["lengths"].copy()
+    L[0] = 1  # Kraft sum > 1
+    L[1] = 1
+    cc["lengths"] = L
+    st, _ = run_decode(ctx, cc, True)
+    assert st == hd.HD_ERR_ARG
+    f = dev_field(c)
+    out = torch.empty(c["n"] + 8, dtype=torch.int16, device="cuda")
+    bad = hd.DeviceField(f.words, f.nbits, f.gap, 96, f.lengths, f.alphabet, f.n)
+    with pytest.raises(hd.HDError) as e:
+        ctx.decode(bad, out)
+    assert e.value.code == hd.HD_ERR_ARG
+    mis = hd.DeviceField(f.words[1:], f.nbits, f.gap, 128, f.lengths, f.alphabet, f.n)
+    with pytest.raises(hd.HDError) as e:
+        ctx.decode(mis, out)
+    assert e.value.code == hd.HD_ERR_ARG
+
+
+@pytest.mark.parametrize("shift", [1, 3, 7])
+def test_unaligned_output(ctx, shift):
+    x = synth.laplace_codes(99991, scale=3.0, seed=15)
+    c = oracle.compress(x, 1024, S=128)
+    f = dev_field(c)
+    buf = torch.full((c["n"] + 32,), CANARY, dtype=torch.int32).to(torch.int16).cuda()
+    ctx.decode(f, buf[shift:])
+    assert ctx.status() == 0
+    r = buf.cpu().numpy().view(np.uint16)
+    assert np.all(r[:shift] == np.uint16(CANARY))
+    assert np.array_equal(r[shift:shift + c["n"]], x)
+    assert np.all(r[shift + c["n"]:] == np.uint16(CANARY))
+
+
+# ---------------------------------------------------------------------------
+# full-size workload: the 512^3 field of Lorenzo codes
+# ---------------------------------------------------------------------------
+
+
+@pytest.fixture(scope="module")
+def cube():
+    x = synth.field3d_codes(512, rel_eb=1e-4, noise=0.01, seed=1001)
+    return x, oracle.compress(x, 1024, S=128)
+
+
+@pytest.mark.parametrize("with_gap", [True, False], ids=["gap", "selfsync"])
+def test_full_512cube(ctx, cube, with_gap):
+    x, c = cube
+    assert c["n"] == 512 ** 3
+    st, res = run_decode(ctx, c, with_gap)
+    assert st == 0
+    assert np.array_equal(res[:c["n"]], x)
+    assert np.all(res[c["n"]:] == np.uint16(CANARY))
+
+
+def test_full_512cube_matches_oracle_decode(ctx, cube):
+    x, c = cube
+    assert np.array_equal(expect(c), x)
