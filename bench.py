@@ -64,7 +64,7 @@ def measured_peak():
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2201_09118_gb300", "csrc")
-    for name in ("decode_gap.cu", "decode_common.cuh", "common.cuh"):
+    for name in ("decode.cu", "decode_common.cuh", "common.cuh"):
         with open(os.path.join(cs, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -222,8 +222,9 @@ def run_gpu(args):
     out = torch.empty(n, dtype=torch.int16, device=f"cuda:{dev}")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
     ctx = hd.Context(dev)
-    if args.threads or args.window or args.lut_bits:
-        ctx.set_config(threads=args.threads, window=args.window, lut_bits=args.lut_bits)
+    if args.threads or args.window or args.lut_bits or args.tiles_per_unit:
+        ctx.set_config(threads=args.threads, window=args.window, lut_bits=args.lut_bits,
+                       tiles_per_unit=args.tiles_per_unit)
     stream = torch.cuda.current_stream()
 
     # correctness of the timed configuration (round trip against the codes)
@@ -341,6 +342,37 @@ def run_gpu(args):
     return 0
 
 
+def run_profile_case(args):
+    """Decodes one strategy `steps` times after `warmup` (for profiler
+    captures); prints one timing line, no bench line."""
+    import torch
+    from paper_2201_09118_gb300 import hd
+    torch.cuda.set_device(0)
+    codes = workload_codes(args.side, seed=1001)
+    n = codes.size
+    lengths = hd.hd_build_codebook(codes, 1024, 32)
+    enc = hd.hd_encode(codes, lengths, 128)
+    f = hd.DeviceField.upload(enc, lengths, n, with_gap=args.profile_strategy == "gap")
+    out = torch.empty(n, dtype=torch.int16, device="cuda")
+    ctx = hd.Context(0)
+    if args.threads or args.window or args.lut_bits or args.tiles_per_unit:
+        ctx.set_config(threads=args.threads, window=args.window, lut_bits=args.lut_bits,
+                       tiles_per_unit=args.tiles_per_unit)
+    for _ in range(args.warmup):
+        ctx.decode(f, out)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.kernel_time()
+    for _ in range(args.steps):
+        ctx.decode(f, out)
+    ms, k = ctx.kernel_time()
+    st = ctx.status()
+    ok = st == 0 and np.array_equal(out.cpu().numpy().view(np.uint16), codes)
+    print(json.dumps({"profile_case": args.profile_strategy, "n_codes": n,
+                      "kernel_ms": ms / max(1, k), "ok": bool(ok)}), flush=True)
+    return 0 if ok else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -351,12 +383,17 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--window", type=int, default=0)
     ap.add_argument("--lut-bits", dest="lut_bits", type=int, default=0)
+    ap.add_argument("--tiles-per-unit", dest="tiles_per_unit", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-strategy", choices=["gap", "selfsync"], default=None,
+                    help="decode one strategy only and print its kernel time (profiler runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_strategy:
+        return run_profile_case(args)
     return run_gpu(args)
 
 
