@@ -159,6 +159,28 @@ int hd_batch_status(hd_ctx* ctx, int32_t* status, uint32_t nf, void* stream);
  * on `stream`; returns when done with the decode status. */
 int hd_decode_host(hd_ctx* ctx, const hd_field* f, uint16_t* host_out, void* stream);
 
+/* Allocation-free gap-array decode.  Some callers cannot call cudaMalloc
+ * when they decode: real-time loops that cannot afford the device-wide
+ * synchronisation cudaMalloc may imply, and plugins or libraries running
+ * inside a host framework whose own allocator has already reserved the device
+ * memory.  This entry point needs no context and allocates nothing.  Its
+ * scratch (control words, look-back states and the decode table) is one fixed
+ * 1 MiB array in device memory that every GPU which loads the library holds
+ * until the process exits.  Arguments are as for hd_decode (device pointers);
+ * the field must carry a gap array (NULL gap -> HD_ERR_ARG).  A field whose
+ * scratch would not fit in the 1 MiB -- about 128,000 work units of 2048
+ * subsequences, i.e. a stream of roughly 4 GB at S = 128 with a 1024-symbol
+ * alphabet -- is rejected with HD_ERR_CAPACITY before any GPU work.  The first
+ * call on each device does a one-time set-up (it looks up the array's device
+ * address with that device current); make that first call before any stream
+ * capture.  All calls on a device share the one array, which keeps the last
+ * call's contents: each call clears the parts that must start at zero, but
+ * calls whose GPU work overlaps (e.g. issued on two streams at once) race on
+ * it and give wrong results.  The call waits for its work on `stream` and
+ * returns the decode status (HD_OK, HD_ERR_CORRUPT, HD_ERR_TIMEOUT, ...).
+ * The paper has no counterpart to this entry point. */
+int hd_decode_static(const hd_field* f, uint16_t* d_out, void* stream);
+
 /* Kernel timing: when enabled, the context records CUDA events around every
  * main decode kernel it launches.  hd_kernel_time waits for them and returns
  * the summed device time in milliseconds and the launch count, then clears. */

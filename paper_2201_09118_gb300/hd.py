@@ -76,6 +76,7 @@ _SIGS = {
     "hd_decode_batch": ([_P, ctypes.POINTER(hd_field), ctypes.c_uint32, _P, _P], ctypes.c_int),
     "hd_batch_status": ([_P, _P, ctypes.c_uint32, _P], ctypes.c_int),
     "hd_decode_host": ([_P, ctypes.POINTER(hd_field), _P, _P], ctypes.c_int),
+    "hd_decode_static": ([ctypes.POINTER(hd_field), _P, _P], ctypes.c_int),
     "hd_profile": ([_P, ctypes.c_int], ctypes.c_int),
     "hd_kernel_time": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
                        ctypes.c_int),
