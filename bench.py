@@ -64,7 +64,7 @@ def measured_peak():
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2201_09118_gb300", "csrc")
-    for name in ("decode.cu", "decode_common.cuh", "common.cuh"):
+    for name in ("decode2.cu", "decode_common.cuh", "common.cuh"):
         with open(os.path.join(cs, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -222,9 +222,9 @@ def run_gpu(args):
     out = torch.empty(n, dtype=torch.int16, device=f"cuda:{dev}")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
     ctx = hd.Context(dev)
-    if args.threads or args.window or args.lut_bits or args.tiles_per_unit:
-        ctx.set_config(threads=args.threads, window=args.window, lut_bits=args.lut_bits,
-                       tiles_per_unit=args.tiles_per_unit)
+    if args.threads or args.window or args.lut_bits or args.scratch_syms or args.subseq_bits:
+        ctx.set_config(subseq_bits=args.subseq_bits, threads=args.threads, window=args.window,
+                       lut_bits=args.lut_bits, scratch_syms=args.scratch_syms)
     stream = torch.cuda.current_stream()
 
     # correctness of the timed configuration (round trip against the codes)
@@ -324,7 +324,7 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}", "launch": ctx.get_config()},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": recorded_traffic("decode_gap", n),
-                     "peak_kind": peak_kind, "kernel": "k_decode_gap",
+                     "peak_kind": peak_kind, "kernel": "k_count + k_write",
                      "kernel_ms": kernel_ms, "algorithmic_bytes": nbytes_alg},
         "e2e": {"value": e2e_gbps, "unit": "GB/s",
                 "h2d_bytes_per_step": int(enc["nwords"] * 4 + enc["nsub"] + 1024),
@@ -355,9 +355,9 @@ def run_profile_case(args):
     f = hd.DeviceField.upload(enc, lengths, n, with_gap=args.profile_strategy == "gap")
     out = torch.empty(n, dtype=torch.int16, device="cuda")
     ctx = hd.Context(0)
-    if args.threads or args.window or args.lut_bits or args.tiles_per_unit:
-        ctx.set_config(threads=args.threads, window=args.window, lut_bits=args.lut_bits,
-                       tiles_per_unit=args.tiles_per_unit)
+    if args.threads or args.window or args.lut_bits or args.scratch_syms or args.subseq_bits:
+        ctx.set_config(subseq_bits=args.subseq_bits, threads=args.threads, window=args.window,
+                       lut_bits=args.lut_bits, scratch_syms=args.scratch_syms)
     for _ in range(args.warmup):
         ctx.decode(f, out)
     torch.cuda.synchronize()
@@ -383,7 +383,8 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--window", type=int, default=0)
     ap.add_argument("--lut-bits", dest="lut_bits", type=int, default=0)
-    ap.add_argument("--tiles-per-unit", dest="tiles_per_unit", type=int, default=0)
+    ap.add_argument("--scratch-syms", dest="scratch_syms", type=int, default=0)
+    ap.add_argument("--subseq-bits", dest="subseq_bits", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-strategy", choices=["gap", "selfsync"], default=None,
                     help="decode one strategy only and print its kernel time (profiler runs)")

@@ -114,9 +114,12 @@ typedef struct hd_field {
 typedef struct hd_config {
   uint32_t subseq_bits; /* decoder subsequence: a multiple of the field's S, <= 256 */
   uint32_t threads;     /* threads per block = subsequences per tile: 128, 256, 512 */
-  uint32_t window;      /* shared-memory output window in symbols (Alg. 1 buffer) */
+  uint32_t window;      /* shared-memory output window in symbols (Alg. 1 buffer);
+                           0 = sized from the field's mean code length */
   uint32_t lut_bits;    /* first-level decode-table index bits, 8 .. 13 */
-  uint32_t tiles_per_unit; /* tiles per look-back step (work unit), 1 .. 16 */
+  uint32_t scratch_syms; /* self-synchronising decode: decoded symbols each thread
+                           keeps in shared memory (a multiple of 8, <= S);
+                           threads with more codewords decode them again */
 } hd_config;
 
 /* Sets the launch shape used by later decodes on this context (NULL resets to
@@ -168,9 +171,10 @@ int hd_decode_host(hd_ctx* ctx, const hd_field* f, uint16_t* host_out, void* str
  * 1 MiB array in device memory that every GPU which loads the library holds
  * until the process exits.  Arguments are as for hd_decode (device pointers);
  * the field must carry a gap array (NULL gap -> HD_ERR_ARG).  A field whose
- * scratch would not fit in the 1 MiB -- about 128,000 work units of 2048
- * subsequences, i.e. a stream of roughly 4 GB at S = 128 with a 1024-symbol
- * alphabet -- is rejected with HD_ERR_CAPACITY before any GPU work.  The first
+ * scratch would not fit in the 1 MiB -- more than about 128,000 tiles of 256
+ * subsequences, i.e. a stream beyond roughly 500 MB at S = 128 with a
+ * 1024-symbol alphabet -- is rejected with HD_ERR_CAPACITY before any GPU
+ * work.  The first
  * call on each device does a one-time set-up (it looks up the array's device
  * address with that device current); make that first call before any stream
  * capture.  All calls on a device share the one array, which keeps the last

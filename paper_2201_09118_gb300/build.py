@@ -44,25 +44,30 @@ def _deps():
         os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__]
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile and link libhd.so if any source changed; returns its path."""
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out_dir: str = None) -> str:
+    """Compile and link libhd.so if any source changed; returns its path.
+
+    ``extra_flags``/``out_dir`` build a variant elsewhere (e.g. the debug build
+    with -DHD_PHASE_TIMERS); the default build goes to _build/libhd.so."""
+    build_dir = out_dir or BUILD
+    lib = os.path.join(build_dir, "libhd.so")
     with _lock:
-        if not force and not _stale():
-            return LIB
-        os.makedirs(os.path.join(BUILD, "obj"), exist_ok=True)
+        if not force and not _stale(lib):
+            return lib
+        os.makedirs(os.path.join(build_dir, "obj"), exist_ok=True)
         cc = nvcc()
         common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                          "-I", INCLUDE, "-I", CSRC, *extra_flags]
 
         def compile_one(src):
-            obj = os.path.join(BUILD, "obj", os.path.basename(src) + ".o")
+            obj = os.path.join(build_dir, "obj", os.path.basename(src) + ".o")
             cmd = [cc, *common, "-c", src, "-o", obj]
             if src.endswith(".cpp"):
                 cmd = [cc, "-x", "cu", *common, "-c", src, "-o", obj]
@@ -76,13 +81,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         srcs = _sources()
         with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
             objs = list(ex.map(compile_one, srcs))
-        tmp = LIB + f".tmp{os.getpid()}"
+        tmp = lib + f".tmp{os.getpid()}"
         r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"],
                            capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
-        return LIB
+        os.replace(tmp, lib)
+        return lib
 
 
 if __name__ == "__main__":

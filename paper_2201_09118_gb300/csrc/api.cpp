@@ -16,6 +16,7 @@
 struct hd_ctx {
   int device = 0;
   int num_sms = 0;
+  int max_smem = 0;  // opt-in shared memory per block (bytes)
   std::mutex mu;
   hd_config cfg{};
   // device workspace (control region, decode tables, field descriptors)
@@ -34,6 +35,7 @@ struct hd_ctx {
   std::vector<cudaEvent_t> events;
   size_t events_used = 0;
   uint64_t launches = 0;
+  hd::LaunchShape last_shape{};  // launch shape of the last decode
 };
 
 namespace {
@@ -43,8 +45,7 @@ using hd::FieldDesc;
 constexpr uint32_t kDefaultThreads = 256;
 constexpr uint32_t kDefaultWindow = 4096;
 constexpr uint32_t kDefaultK = 12;
-constexpr uint32_t kDefaultM = 8;
-constexpr uint64_t kTimeoutNs = 2000000000ull;
+constexpr uint64_t kTimeoutCycles = 4000000000ull;  // ~2 s at GB300 clocks
 
 struct DeviceGuard {
   int prev = -1;
@@ -119,21 +120,41 @@ int check_field(const hd_field* f, bool need_out, const void* out) {
   return HD_OK;
 }
 
-hd::LaunchShape shape_for(const hd_ctx* c, uint32_t stream_S) {
+// Scratch symbols per thread: room for about 1.5x the expected codewords of a
+// subsequence (from the field's mean code length), a multiple of 8, <= S.
+uint32_t default_cmax(uint32_t S, uint64_t nbits, uint64_t n) {
+  double per = n ? static_cast<double>(S) * static_cast<double>(n) /
+                       static_cast<double>(nbits ? nbits : 1)
+                 : 8.0;
+  uint32_t c = static_cast<uint32_t>(per * 1.35 + 4.0);
+  c = (c + 7) / 8 * 8;
+  if (c < 8) c = 8;
+  if (c > S) c = S;
+  return c;
+}
+
+// Decoder subsequence when the configuration leaves it open: gap-array
+// decodes take 256-bit subsequences (every second gap entry of a 128-bit
+// stream) because the per-tile work of a thread then amortises its fixed
+// costs better; the synchronising kernel uses the stream's own size.
+uint32_t default_decoder_S(uint32_t stream_S, bool gap) {
+  if (!gap) return stream_S;
+  return stream_S < 256 ? 256 : stream_S;
+}
+
+hd::LaunchShape shape_for(const hd_ctx* c, uint32_t stream_S, bool gap) {
   hd::LaunchShape s{};
-  s.S = c->cfg.subseq_bits ? c->cfg.subseq_bits : stream_S;
+  s.S = c->cfg.subseq_bits ? c->cfg.subseq_bits : default_decoder_S(stream_S, gap);
   s.threads = c->cfg.threads ? c->cfg.threads : kDefaultThreads;
   s.K = c->cfg.lut_bits ? c->cfg.lut_bits : kDefaultK;
-  s.window = std::max(c->cfg.window ? c->cfg.window : kDefaultWindow, s.S);
-  s.window = static_cast<uint32_t>(align_up(s.window, 8));
-  s.M = c->cfg.tiles_per_unit ? c->cfg.tiles_per_unit : kDefaultM;
+  s.window = c->cfg.window;  // 0: chosen per launch
+  s.cmax = c->cfg.scratch_syms;  // 0: chosen per launch
   s.grid = 0;
   return s;
 }
 
-uint64_t units_for(uint64_t nsub, const hd::LaunchShape& s) {
-  const uint64_t per = static_cast<uint64_t>(s.threads) * s.M;
-  return (nsub + per - 1) / per;
+uint64_t tiles_for(uint64_t nsub, const hd::LaunchShape& s) {
+  return (nsub + s.threads - 1) / s.threads;
 }
 
 cudaEvent_t next_event(hd_ctx* c) {
@@ -160,25 +181,72 @@ void fill_desc(FieldDesc& d, const hd_field* f, const hd::LaunchShape& s, uint16
   d.n = f->n;
 }
 
-// Queues decode-table build + control clear + decode kernels for fields that
-// all use the same strategy (gap array or self-synchronisation).
-int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape& s,
+// Queues the decode-table build (which also clears the per-launch control
+// region) and the decode kernels for fields that all use the same strategy:
+// gap array -> count kernel + decode-and-write kernel; self-synchronisation
+// -> the synchronising decode kernel (or, with sync_only, the gap arrays).
+int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape& shape,
                  bool self_sync, bool sync_only, cudaStream_t st) {
   const uint32_t nf = static_cast<uint32_t>(descs.size());
-  uint64_t total_units = 0;
+  hd::LaunchShape s = shape;
+  const bool two_phase = !self_sync;
+  double bits_per = 0;
+  uint32_t amax = 0;
   for (auto& d : descs) {
-    d.unit_begin = total_units;
-    d.nunits = units_for(d.nsub, s);
-    total_units += d.nunits;
+    bits_per = std::max(bits_per, static_cast<double>(d.nbits) / static_cast<double>(d.n ? d.n : 1));
+    amax = std::max(amax, d.alphabet);
   }
-  // workspace layout
+  // symbols of codes longer than the first-level table, kept in shared memory
+  s.long_cap = static_cast<uint32_t>(align_up(std::min<uint32_t>(amax, 4096), 8));
+  if (s.window == 0) {
+    // output window: about 1.2x a tile's expected symbol count
+    const double want = two_phase ? 1.2 * s.threads * s.S / std::max(bits_per, 0.25) + 64.0
+                                  : static_cast<double>(kDefaultWindow);
+    s.window = static_cast<uint32_t>(std::min(std::max(want, 1024.0), 16384.0));
+  }
+  s.window = static_cast<uint32_t>(align_up(std::max(s.window, s.S), 8));
+  if (s.cmax == 0) {
+    for (auto& d : descs) s.cmax = std::max(s.cmax, default_cmax(s.S, d.nbits, d.n));
+  }
+  s.cmax = std::min(s.cmax, s.S);
+  {
+    // the window and the synchronising kernel's scratch are optimisations
+    // (larger outputs go through several windows, threads whose codewords do
+    // not fit the scratch decode twice), so they shrink to fit shared memory
+    auto smem_of = [&](const hd::LaunchShape& x) {
+      return two_phase ? hd::two_phase_smem_bytes(x) : hd::decode_smem_bytes(x, self_sync);
+    };
+    const size_t budget = static_cast<size_t>(c->max_smem) - 2048;
+    while (s.window > std::max<uint32_t>(1024, s.S) && smem_of(s) > budget) s.window -= 512;
+    if (!two_phase) {
+      hd::LaunchShape z = s;
+      z.cmax = 0;
+      const size_t fixed = smem_of(z);
+      if (fixed + 16ull * s.threads > budget) return HD_ERR_ARG;
+      const size_t fit = (budget - fixed) / (2ull * s.threads) / 8 * 8;
+      s.cmax = static_cast<uint32_t>(std::min<size_t>(s.cmax, fit));
+      if (s.cmax < 8) s.cmax = 8;
+    }
+    if (smem_of(s) > budget) return HD_ERR_ARG;
+  }
+  uint64_t total_tiles = 0, total_sub = 0;
+  for (auto& d : descs) {
+    d.unit_begin = total_tiles;
+    d.nunits = tiles_for(d.nsub, s);
+    total_tiles += d.nunits;
+    d.count_begin = total_sub;
+    total_sub += d.nsub;
+  }
+  // workspace layout; [0, zero_bytes) is cleared by the table kernel
   size_t off = 0;
   const size_t ctrl_off = off;  // ticket, abort flag
   off += 16;
   const size_t err_off = off;
   off = align_up(off + 4ull * nf, 16);
-  const size_t state_off = off;
-  off = align_up(off + 8ull * total_units, 16);
+  const size_t state_off = off;  // look-back states (synchronising kernel)
+  if (!two_phase) off = align_up(off + 8ull * total_tiles, 16);
+  const size_t seg_off = off;  // segment totals (two-phase)
+  if (two_phase) off = align_up(off + 8ull * ((total_tiles + 255) / 256 + 1), 16);
   const size_t zero_bytes = off;
   off = align_up(off, 256);
   std::vector<size_t> tab_off(nf);
@@ -188,6 +256,10 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
   }
   const size_t desc_off = align_up(off, 256);
   off = desc_off + (nf > 1 ? sizeof(FieldDesc) * nf : 0);
+  const size_t tile_off = align_up(off, 256);
+  off = tile_off + (two_phase ? 4ull * total_tiles : 0);
+  const size_t count_off = align_up(off, 256);
+  off = count_off + (two_phase ? hd::count_bytes_per_subsequence(s.S) * total_sub : 0);
   int rc = ensure_ws(c, off);
   if (rc) return rc;
   char* ws = c->ws;
@@ -221,24 +293,30 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
   dp.K = s.K;
   dp.window = s.window;
   dp.sync_only = sync_only ? 1u : 0u;
-  dp.M = s.M;
-  dp.total_units = total_units;
+  dp.cmax = s.cmax;
+  dp.long_cap = s.long_cap;
+  dp.total_units = total_tiles;
   dp.unit_state = reinterpret_cast<uint64_t*>(ws + state_off);
   dp.ticket = reinterpret_cast<uint32_t*>(ws + ctrl_off);
   dp.abort_flag = reinterpret_cast<uint32_t*>(ws + ctrl_off) + 1;
-  dp.timeout_ns = kTimeoutNs;
+  dp.timeout_cycles = kTimeoutCycles;
+  dp.counts = ws + count_off;
+  dp.tile_total = reinterpret_cast<uint32_t*>(ws + tile_off);
+  dp.seg_total = reinterpret_cast<uint64_t*>(ws + seg_off);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->profile) {
     e0 = next_event(c);
     e1 = next_event(c);
     cudaEventRecord(e0, st);
   }
-  e = hd::launch_decode(dp, s, self_sync, c->num_sms, st);
+  e = two_phase ? hd::launch_decode_two_phase(dp, s, c->num_sms, st)
+                : hd::launch_decode(dp, s, self_sync, c->num_sms, st);
   if (c->profile) cudaEventRecord(e1, st);
   if (e != cudaSuccess) return HD_ERR_CUDA;
-  c->launches += 1;
+  c->launches += two_phase ? 2 : 1;
   c->err_off = err_off;
   c->err_count = nf;
+  c->last_shape = s;
   return HD_OK;
 }
 
@@ -278,7 +356,9 @@ int hd_ctx_create(int device, hd_ctx** out) {
   c->device = device;
   DeviceGuard g(device);
   if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) !=
-      cudaSuccess) {
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) !=
+          cudaSuccess) {
     delete c;
     return HD_ERR_CUDA;
   }
@@ -306,12 +386,12 @@ int hd_set_config(hd_ctx* c, const hd_config* cfg) {
     c->cfg = hd_config{};
     return HD_OK;
   }
-  if (cfg->subseq_bits && !valid_S(cfg->subseq_bits)) return HD_ERR_ARG;
+  if (cfg->subseq_bits && !valid_S(cfg->subseq_bits) && cfg->subseq_bits != 512) return HD_ERR_ARG;
   if (cfg->threads && cfg->threads != 128 && cfg->threads != 256 && cfg->threads != 512)
     return HD_ERR_ARG;
   if (cfg->lut_bits && (cfg->lut_bits < 8 || cfg->lut_bits > 13)) return HD_ERR_ARG;
   if (cfg->window && (cfg->window < 64 || cfg->window > 32768)) return HD_ERR_ARG;
-  if (cfg->tiles_per_unit > hd::kMaxTilesPerUnit) return HD_ERR_ARG;
+  if (cfg->scratch_syms && (cfg->scratch_syms % 8 || cfg->scratch_syms > 256)) return HD_ERR_ARG;
   c->cfg = *cfg;
   return HD_OK;
 }
@@ -321,9 +401,9 @@ int hd_get_config(hd_ctx* c, hd_config* cfg) {
   std::lock_guard<std::mutex> lk(c->mu);
   cfg->subseq_bits = c->cfg.subseq_bits;
   cfg->threads = c->cfg.threads ? c->cfg.threads : kDefaultThreads;
-  cfg->window = c->cfg.window ? c->cfg.window : kDefaultWindow;
+  cfg->window = c->cfg.window ? c->cfg.window : c->last_shape.window;
   cfg->lut_bits = c->cfg.lut_bits ? c->cfg.lut_bits : kDefaultK;
-  cfg->tiles_per_unit = c->cfg.tiles_per_unit ? c->cfg.tiles_per_unit : kDefaultM;
+  cfg->scratch_syms = c->cfg.scratch_syms;
   return HD_OK;
 }
 
@@ -344,8 +424,9 @@ static int decode_impl(hd_ctx* c, const hd_field* f, uint16_t* d_out, uint8_t* g
     c->host_status = HD_ERR_CORRUPT;  // symbols without bits or bits without symbols
     return HD_OK;
   }
-  hd::LaunchShape s = shape_for(c, f->subseq_bits);
   const bool self_sync = sync_only || f->gap == nullptr;
+  hd::LaunchShape s = shape_for(c, f->subseq_bits, !self_sync);
+  if (self_sync && s.S > 256) s.S = 256;  // the synchronising kernel stops at 256-bit subsequences
   if (!self_sync && (s.S % f->subseq_bits)) {
     c->host_status = HD_ERR_ARG;
     return HD_ERR_ARG;
@@ -409,7 +490,9 @@ int hd_decode_batch(hd_ctx* c, const hd_field* fs, uint32_t nf, uint16_t* const*
     }
     maxS = std::max(maxS, fs[i].subseq_bits);
   }
-  hd::LaunchShape s = shape_for(c, maxS ? maxS : 128);
+  bool all_gap = true;
+  for (uint32_t i = 0; i < nf; ++i) all_gap &= fs[i].gap != nullptr;
+  hd::LaunchShape s = shape_for(c, maxS ? maxS : 128, all_gap);
   std::vector<FieldDesc> gap_d, sync_d;
   std::vector<uint32_t> gap_i, sync_i;
   for (uint32_t i = 0; i < nf; ++i) {

@@ -7,7 +7,6 @@
 namespace hd {
 
 constexpr uint32_t kMaxCodeLen = 32;
-constexpr uint32_t kMaxTilesPerUnit = 16;
 constexpr uint32_t kTableHeaderBytes = 512;
 
 // Decode-table header, written by the table kernel, followed in memory by the
@@ -26,6 +25,7 @@ struct TableHeader {
   uint32_t K;        // first-level index bits
   uint64_t end[34];  // end[L]: exclusive left-aligned limit of codes of length <= L
   uint32_t base[34]; // start[L] - first[L] (mod 2^32): rank = (w >> (32-L)) + base[L]
+  uint32_t long0;    // rank of the first code longer than K (codes sorted by length)
 };
 static_assert(sizeof(TableHeader) <= kTableHeaderBytes, "table header too large");
 
@@ -49,10 +49,11 @@ struct FieldDesc {
   const TableHeader* table;// decode table built from `lengths`
   uint16_t* out;           // decoded symbols [n]
   uint64_t n;              // expected symbol count
-  uint64_t unit_begin;     // index of this field's first work unit in the launch
-  uint64_t nunits;         // work units of this field
+  uint64_t unit_begin;     // index of this field's first tile in the launch
+  uint64_t nunits;         // tiles of this field
   uint32_t* err;           // error bits of this field
   uint8_t* gap_out;        // sync-point mode: gap array written here
+  uint64_t count_begin;    // first entry of this field's per-subsequence counts
 };
 
 // Error bits (per field).
@@ -72,13 +73,16 @@ struct DecodeParams {
   uint32_t K;               // first-level table bits for this launch
   uint32_t window;          // shared-memory output window, symbols (Alg. 1 buffer)
   uint32_t sync_only;       // 1: write gap arrays, do not decode
-  uint32_t M;               // tiles of B subsequences per work unit (1 .. kMaxTilesPerUnit)
-  uint32_t pad0;
-  uint64_t total_units;
-  uint64_t* unit_state;     // look-back state per work unit (zeroed before launch)
-  uint32_t* ticket;         // dynamic work-unit counter (zeroed before launch)
+  uint32_t cmax;            // scratch symbols per subsequence (<= S)
+  uint32_t long_cap;        // sorted symbols of long codes kept in shared memory
+  uint64_t total_units;     // tiles in the launch
+  uint64_t* unit_state;     // look-back state per tile (zeroed before launch)
+  uint32_t* ticket;         // dynamic tile counter (zeroed before launch)
   uint32_t* abort_flag;     // set when any wait times out (zeroed before launch)
-  uint64_t timeout_ns;      // per-wait limit
+  uint64_t timeout_cycles;  // per-wait limit in SM clock cycles
+  void* counts;             // two-phase decode: codewords per subsequence (u8, or u16 for S=256)
+  uint32_t* tile_total;     // two-phase decode: codewords per tile
+  uint64_t* seg_total;      // two-phase decode: codewords per 256 tiles (zeroed before launch)
 };
 
 struct PrepParams {

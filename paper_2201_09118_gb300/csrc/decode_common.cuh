@@ -48,7 +48,10 @@ struct Tables {
   const uint32_t* lut;
   const uint64_t* end;
   const uint32_t* base;
-  const uint16_t* sorted;
+  const uint16_t* sorted;    // all symbols by (length, symbol), global memory
+  const uint16_t* long_syms; // shared-memory copy of sorted[long0 ..], long_cap entries
+  uint32_t long0;
+  uint32_t long_cap;
   uint32_t maxlen;
   uint32_t shift;  // 32 - K
 };
@@ -92,7 +95,9 @@ __device__ __forceinline__ uint32_t code_sym(const Tables& T, uint32_t w, uint32
     sym = 0;
     return 1;
   }
-  sym = __ldg(T.sorted + ((w >> (32 - L)) + T.base[L]));
+  const uint32_t rank = (w >> (32 - L)) + T.base[L];
+  const uint32_t li = rank - T.long0;
+  sym = li < T.long_cap ? T.long_syms[li] : __ldg(T.sorted + rank);
   return L;
 }
 
@@ -131,16 +136,16 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
   return v;
 }
 
-// Waits a little; returns false once the launch was aborted or the wait
-// started at t0 exceeded the limit (the caller records a timeout and stops
-// waiting).
+// One more round of a spin-wait that began at t0 (an SM cycle count).  The
+// caller re-reads global state between rounds, which paces the spin; this
+// returns false once the launch was aborted or the wait exceeded its limit
+// (the caller then records a timeout and stops waiting).
 __device__ __forceinline__ bool backoff_wait(const DecodeParams& P, uint64_t t0) {
   if (ld_relaxed32(P.abort_flag)) return false;
-  if (now_ns() - t0 > P.timeout_ns) {
+  if (static_cast<uint64_t>(clock64()) - t0 > P.timeout_cycles) {
     atomicExch(P.abort_flag, 1u);
     return false;
   }
-  __nanosleep(64);
   return true;
 }
 
@@ -161,7 +166,7 @@ __device__ __forceinline__ uint64_t lookback_counts(const DecodeParams& P, uint6
   uint64_t excl = 0;
   int64_t j = static_cast<int64_t>(g) - 1;
   const int64_t lo = static_cast<int64_t>(first_unit);
-  const uint64_t t0 = now_ns();
+  const uint64_t t0 = static_cast<uint64_t>(clock64());
   for (;;) {
     const int64_t idx = j - lane;
     const uint64_t s = idx >= lo ? ld_relaxed(st + idx) : kStateInc;
@@ -241,10 +246,13 @@ __device__ __forceinline__ void window_write(uint16_t* s_out, uint32_t* s_flush_
   }
 }
 
-// Loads the decode table of a field into shared memory (whole block).
+// Loads the decode table of a field into shared memory (threads [0, nthreads)):
+// the first-level table, the per-length limits and the first long_cap symbols
+// of codes longer than K.  s_meta = {maxlen, status, long0}.
 __device__ __forceinline__ void load_table(const TableHeader* H, uint32_t K, uint32_t* s_lut,
                                            uint64_t* s_end, uint32_t* s_base,
-                                           uint32_t* s_meta, int nthreads) {
+                                           uint32_t* s_meta, int nthreads,
+                                           uint16_t* s_long = nullptr, uint32_t long_cap = 0) {
   const int t = threadIdx.x;
   const uint4* src =
       reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(H) + kTableHeaderBytes);
@@ -258,6 +266,14 @@ __device__ __forceinline__ void load_table(const TableHeader* H, uint32_t K, uin
   if (t == 0) {
     s_meta[0] = H->maxlen;
     s_meta[1] = H->status;
+    s_meta[2] = H->long0;
+  }
+  if (long_cap) {
+    const uint16_t* sorted = reinterpret_cast<const uint16_t*>(
+        reinterpret_cast<const char*>(H) + kTableHeaderBytes + (4u << K));
+    const uint32_t nused = H->nused, l0 = H->long0;
+    const uint32_t nl = nused > l0 ? nused - l0 : 0u;
+    for (uint32_t k = t; k < long_cap; k += nthreads) s_long[k] = k < nl ? sorted[l0 + k] : 0;
   }
 }
 

@@ -22,12 +22,23 @@ struct LaunchShape {
   uint32_t threads;  // threads per block = subsequences per tile
   uint32_t window;   // output window (symbols)
   uint32_t K;        // table bits
-  uint32_t M;        // tiles per work unit (look-back granularity)
+  uint32_t cmax;     // scratch symbols per subsequence
+  uint32_t long_cap; // symbols of long codes kept in shared memory
   uint32_t grid;     // persistent blocks (0: full occupancy)
 };
 
 // Dynamic shared memory one decode block needs for a launch shape.
 size_t decode_smem_bytes(const LaunchShape& s, bool self_sync);
+
+// Two-phase gap-array decode (count kernel, then decode-and-write kernel).
+cudaError_t launch_decode_two_phase(const DecodeParams& p, const LaunchShape& s, int num_sms,
+                                    cudaStream_t stream);
+
+// Dynamic shared memory of the decode-and-write kernel (s.window = window).
+size_t two_phase_smem_bytes(const LaunchShape& s);
+
+// Bytes per stored codeword count for subsequences of S bits.
+size_t count_bytes_per_subsequence(uint32_t S);
 
 // Decodes all fields of `p` with the gap-array variant (Sec. III-C) or the
 // self-synchronising variant (Sec. III-B, IV-A); with p.sync_only the latter

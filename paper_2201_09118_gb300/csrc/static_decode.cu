@@ -25,10 +25,18 @@ int g_num_sms[kMaxDevices] = {};
 constexpr uint32_t kThreads = 256;
 constexpr uint32_t kWindow = 4096;
 constexpr uint32_t kLutBits = 12;
-constexpr uint32_t kTilesPerUnit = 8;
-constexpr uint64_t kTimeoutNs = 2000000000ull;
+constexpr uint64_t kTimeoutCycles = 4000000000ull;  // ~2 s at GB300 clocks
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Scratch symbols per thread: about 1.5x the expected codewords of a
+// subsequence, a multiple of 8, at most S.
+uint32_t scratch_syms(uint32_t S, uint64_t nbits, uint64_t n) {
+  const double per = static_cast<double>(S) * static_cast<double>(n) / static_cast<double>(nbits);
+  uint32_t c = static_cast<uint32_t>(per * 1.35 + 4.0);
+  c = (c + 7) / 8 * 8;
+  return c > S ? S : c;
+}
 
 // One-time set-up on the current device: the device address of the scratch
 // array (host code may not use the symbol itself) and the SM count.
@@ -71,13 +79,13 @@ extern "C" int hd_decode_static(const hd_field* f, uint16_t* d_out, void* stream
   s.threads = kThreads;
   s.window = kWindow;
   s.K = kLutBits;
-  s.M = kTilesPerUnit;
+  s.cmax = scratch_syms(s.S, f->nbits, f->n);
+  s.long_cap = ((f->alphabet < 4096 ? f->alphabet : 4096u) + 7u) / 8 * 8;
   s.grid = 0;
   const uint64_t nsub = (f->nbits + s.S - 1) / s.S;
-  const uint64_t per_unit = static_cast<uint64_t>(s.threads) * s.M;
-  const uint64_t units = (nsub + per_unit - 1) / per_unit;
+  const uint64_t units = (nsub + s.threads - 1) / s.threads;  // tiles
 
-  // scratch layout: ticket, abort flag, error word | unit states | table
+  // scratch layout: ticket, abort flag, error word | tile states | table
   const size_t err_off = 8;
   const size_t state_off = 16;
   const size_t zero_bytes = round_up(state_off + 8 * units, 16);
@@ -130,12 +138,13 @@ extern "C" int hd_decode_static(const hd_field* f, uint16_t* d_out, void* stream
   dp.K = s.K;
   dp.window = s.window;
   dp.sync_only = 0;
-  dp.M = s.M;
+  dp.cmax = s.cmax;
+  dp.long_cap = s.long_cap;
   dp.total_units = units;
   dp.unit_state = reinterpret_cast<uint64_t*>(scratch + state_off);
   dp.ticket = reinterpret_cast<uint32_t*>(scratch);
   dp.abort_flag = reinterpret_cast<uint32_t*>(scratch) + 1;
-  dp.timeout_ns = kTimeoutNs;
+  dp.timeout_cycles = kTimeoutCycles;
   if (hd::launch_decode(dp, s, false, num_sms, st) != cudaSuccess) return HD_ERR_CUDA;
 
   uint32_t bits = 0;

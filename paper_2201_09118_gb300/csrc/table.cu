@@ -86,6 +86,7 @@ __device__ void build_table(const FieldDesc& F, uint32_t K) {
     H->maxlen = s_maxlen;
     H->nused = s_nused;
     H->K = K;
+    H->long0 = s_start[K + 1 <= 33 ? K + 1 : 33];
     for (int L = 0; L < 34; ++L) {
       H->end[L] = s_end[L];
       H->base[L] = s_base[L];

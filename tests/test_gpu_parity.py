@@ -95,15 +95,15 @@ def test_launch_shapes(ctx, S, threads, with_gap):
     x = synth.laplace_codes(200003, scale=30.0, seed=S + threads)
     c = oracle.compress(x, 1024, S=S)
     try:
-        for window, K, M in ((S, 8, 1), (1024, 11, 2), (4096, 12, 8), (8192, 13, 16)):
-            ctx.set_config(subseq_bits=S, threads=threads, window=max(window, S), lut_bits=K,
-                           tiles_per_unit=M)
+        for window, K, cm in ((S, 8, 8), (1024, 11, 16), (0, 12, 0), (8192, 13, S)):
+            ctx.set_config(subseq_bits=S, threads=threads, window=max(window, S) if window else 0,
+                           lut_bits=K, scratch_syms=cm)
             check(ctx, c, with_gap)
     finally:
         ctx.reset_config()
 
 
-@pytest.mark.parametrize("dec_S", [128, 256])
+@pytest.mark.parametrize("dec_S", [128, 256, 512])
 def test_decoder_subsequence_multiple_of_stream(ctx, dec_S):
     x = synth.laplace_codes(100000, scale=3.0, seed=5)
     c = oracle.compress(x, 1024, S=64)
