@@ -43,7 +43,6 @@ namespace {
 using hd::FieldDesc;
 
 constexpr uint32_t kDefaultThreads = 256;
-constexpr uint32_t kDefaultWindow = 4096;
 constexpr uint32_t kDefaultK = 12;
 constexpr uint64_t kTimeoutCycles = 4000000000ull;  // ~2 s at GB300 clocks
 
@@ -120,19 +119,6 @@ int check_field(const hd_field* f, bool need_out, const void* out) {
   return HD_OK;
 }
 
-// Scratch symbols per thread: room for about 1.5x the expected codewords of a
-// subsequence (from the field's mean code length), a multiple of 8, <= S.
-uint32_t default_cmax(uint32_t S, uint64_t nbits, uint64_t n) {
-  double per = n ? static_cast<double>(S) * static_cast<double>(n) /
-                       static_cast<double>(nbits ? nbits : 1)
-                 : 8.0;
-  uint32_t c = static_cast<uint32_t>(per * 1.35 + 4.0);
-  c = (c + 7) / 8 * 8;
-  if (c < 8) c = 8;
-  if (c > S) c = S;
-  return c;
-}
-
 // Decoder subsequence when the configuration leaves it open: gap-array
 // decodes take 256-bit subsequences (every second gap entry of a 128-bit
 // stream) because the per-tile work of a thread then amortises its fixed
@@ -183,13 +169,14 @@ void fill_desc(FieldDesc& d, const hd_field* f, const hd::LaunchShape& s, uint16
 
 // Queues the decode-table build (which also clears the per-launch control
 // region) and the decode kernels for fields that all use the same strategy:
-// gap array -> count kernel + decode-and-write kernel; self-synchronisation
-// -> the synchronising decode kernel (or, with sync_only, the gap arrays).
+//   gap array            count kernel, decode-and-write kernel;
+//   self-synchronisation synchronising kernel, link-fix kernel, then the same
+//                        decode-and-write kernel (with sync_only: the first two
+//                        alone, which leave the gap arrays in each gap_out).
 int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape& shape,
                  bool self_sync, bool sync_only, cudaStream_t st) {
   const uint32_t nf = static_cast<uint32_t>(descs.size());
   hd::LaunchShape s = shape;
-  const bool two_phase = !self_sync;
   double bits_per = 0;
   uint32_t amax = 0;
   for (auto& d : descs) {
@@ -200,34 +187,19 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
   s.long_cap = static_cast<uint32_t>(align_up(std::min<uint32_t>(amax, 4096), 8));
   if (s.window == 0) {
     // output window: about 1.2x a tile's expected symbol count
-    const double want = two_phase ? 1.2 * s.threads * s.S / std::max(bits_per, 0.25) + 64.0
-                                  : static_cast<double>(kDefaultWindow);
+    const double want = 1.2 * s.threads * s.S / std::max(bits_per, 0.25) + 64.0;
     s.window = static_cast<uint32_t>(std::min(std::max(want, 1024.0), 16384.0));
   }
   s.window = static_cast<uint32_t>(align_up(std::max(s.window, s.S), 8));
-  if (s.cmax == 0) {
-    for (auto& d : descs) s.cmax = std::max(s.cmax, default_cmax(s.S, d.nbits, d.n));
-  }
-  s.cmax = std::min(s.cmax, s.S);
+  s.cmax = 0;
   {
-    // the window and the synchronising kernel's scratch are optimisations
-    // (larger outputs go through several windows, threads whose codewords do
-    // not fit the scratch decode twice), so they shrink to fit shared memory
-    auto smem_of = [&](const hd::LaunchShape& x) {
-      return two_phase ? hd::two_phase_smem_bytes(x) : hd::decode_smem_bytes(x, self_sync);
-    };
+    // the window is an optimisation (larger outputs go through several
+    // windows), so it shrinks to fit shared memory
     const size_t budget = static_cast<size_t>(c->max_smem) - 2048;
-    while (s.window > std::max<uint32_t>(1024, s.S) && smem_of(s) > budget) s.window -= 512;
-    if (!two_phase) {
-      hd::LaunchShape z = s;
-      z.cmax = 0;
-      const size_t fixed = smem_of(z);
-      if (fixed + 16ull * s.threads > budget) return HD_ERR_ARG;
-      const size_t fit = (budget - fixed) / (2ull * s.threads) / 8 * 8;
-      s.cmax = static_cast<uint32_t>(std::min<size_t>(s.cmax, fit));
-      if (s.cmax < 8) s.cmax = 8;
-    }
-    if (smem_of(s) > budget) return HD_ERR_ARG;
+    while (s.window > std::max<uint32_t>(1024, s.S) && hd::two_phase_smem_bytes(s) > budget)
+      s.window -= 512;
+    if (hd::two_phase_smem_bytes(s) > budget) return HD_ERR_ARG;
+    if (self_sync && hd::sync_smem_bytes(s) > budget) return HD_ERR_ARG;
   }
   uint64_t total_tiles = 0, total_sub = 0;
   for (auto& d : descs) {
@@ -243,10 +215,8 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
   off += 16;
   const size_t err_off = off;
   off = align_up(off + 4ull * nf, 16);
-  const size_t state_off = off;  // look-back states (synchronising kernel)
-  if (!two_phase) off = align_up(off + 8ull * total_tiles, 16);
-  const size_t seg_off = off;  // segment totals (two-phase)
-  if (two_phase) off = align_up(off + 8ull * ((total_tiles + 255) / 256 + 1), 16);
+  const size_t seg_off = off;  // codewords per 256 tiles
+  off = align_up(off + 8ull * ((total_tiles + 255) / 256 + 1), 16);
   const size_t zero_bytes = off;
   off = align_up(off, 256);
   std::vector<size_t> tab_off(nf);
@@ -257,15 +227,29 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
   const size_t desc_off = align_up(off, 256);
   off = desc_off + (nf > 1 ? sizeof(FieldDesc) * nf : 0);
   const size_t tile_off = align_up(off, 256);
-  off = tile_off + (two_phase ? 4ull * total_tiles : 0);
+  off = tile_off + 4ull * total_tiles;
   const size_t count_off = align_up(off, 256);
-  off = count_off + (two_phase ? hd::count_bytes_per_subsequence(s.S) * total_sub : 0);
+  off = count_off + hd::count_bytes_per_subsequence(s.S) * total_sub;
+  // self-synchronisation: subsequence starts, tile links (16-byte padded)
+  const size_t link_bytes = align_up(total_tiles + 1, 16) + 16;
+  const size_t gap_off = align_up(off, 256);
+  if (self_sync && !sync_only) off = gap_off + total_sub;
+  const size_t ta_off = align_up(off, 256);
+  const size_t te_off = align_up(ta_off + link_bytes, 256);
+  const size_t tf_off = align_up(te_off + link_bytes, 256);
+  if (self_sync) off = tf_off + total_tiles;
   int rc = ensure_ws(c, off);
   if (rc) return rc;
   char* ws = c->ws;
   for (uint32_t k = 0; k < nf; ++k) {
-    descs[k].table = reinterpret_cast<const hd::TableHeader*>(ws + tab_off[k]);
-    descs[k].err = reinterpret_cast<uint32_t*>(ws + err_off) + k;
+    FieldDesc& d = descs[k];
+    d.table = reinterpret_cast<const hd::TableHeader*>(ws + tab_off[k]);
+    d.err = reinterpret_cast<uint32_t*>(ws + err_off) + k;
+    if (self_sync) {
+      if (!sync_only) d.gap_out = reinterpret_cast<uint8_t*>(ws + gap_off) + d.count_begin;
+      d.gap = d.gap_out;
+      d.gap_stride = 1;
+    }
   }
   cudaError_t e = cudaSuccess;
   if (nf > 1) {
@@ -296,24 +280,32 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
   dp.cmax = s.cmax;
   dp.long_cap = s.long_cap;
   dp.total_units = total_tiles;
-  dp.unit_state = reinterpret_cast<uint64_t*>(ws + state_off);
   dp.ticket = reinterpret_cast<uint32_t*>(ws + ctrl_off);
   dp.abort_flag = reinterpret_cast<uint32_t*>(ws + ctrl_off) + 1;
   dp.timeout_cycles = kTimeoutCycles;
   dp.counts = ws + count_off;
   dp.tile_total = reinterpret_cast<uint32_t*>(ws + tile_off);
   dp.seg_total = reinterpret_cast<uint64_t*>(ws + seg_off);
+  if (self_sync) {
+    dp.tile_a = reinterpret_cast<uint8_t*>(ws + ta_off);
+    dp.tile_e = reinterpret_cast<uint8_t*>(ws + te_off);
+    dp.tile_flag = reinterpret_cast<uint8_t*>(ws + tf_off);
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->profile) {
     e0 = next_event(c);
     e1 = next_event(c);
     cudaEventRecord(e0, st);
   }
-  e = two_phase ? hd::launch_decode_two_phase(dp, s, c->num_sms, st)
-                : hd::launch_decode(dp, s, self_sync, c->num_sms, st);
+  if (self_sync) {
+    e = hd::launch_sync(dp, s, c->num_sms, st);
+    if (e == cudaSuccess && !sync_only) e = hd::launch_write(dp, s, c->num_sms, st);
+  } else {
+    e = hd::launch_decode_two_phase(dp, s, c->num_sms, st);
+  }
   if (c->profile) cudaEventRecord(e1, st);
   if (e != cudaSuccess) return HD_ERR_CUDA;
-  c->launches += two_phase ? 2 : 1;
+  c->launches += self_sync ? (sync_only ? 2 : 3) : 2;
   c->err_off = err_off;
   c->err_count = nf;
   c->last_shape = s;

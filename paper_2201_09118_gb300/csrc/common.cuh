@@ -83,6 +83,9 @@ struct DecodeParams {
   void* counts;             // two-phase decode: codewords per subsequence (u8, or u16 for S=256)
   uint32_t* tile_total;     // two-phase decode: codewords per tile
   uint64_t* seg_total;      // two-phase decode: codewords per 256 tiles (zeroed before launch)
+  uint8_t* tile_a;          // self-synchronisation: start offset each tile assumed
+  uint8_t* tile_e;          // self-synchronisation: tile_e[g + 1] = where tile g stopped, minus S
+  uint8_t* tile_flag;       // self-synchronisation: 1 = last subsequence overran nbits
 };
 
 struct PrepParams {

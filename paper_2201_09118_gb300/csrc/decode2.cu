@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(B) k_write(const __grid_constant__ DecodeParam
                         p += code_sym(T, peek<B>(col, p), sym, bad);
                         dst[j] = static_cast<uint16_t>(sym);
                       }
+                      if (bad) atomicOr(F.err, kErrCode);
                     });
   }
 }
@@ -262,6 +263,18 @@ cudaError_t launch_s(const DecodeParams& p, const LaunchShape& s, int num_sms,
   }
 }
 
+template <int S>
+cudaError_t launch_write_s(const DecodeParams& p, const LaunchShape& s, int num_sms,
+                           cudaStream_t stream) {
+  const size_t smem = two_phase_smem_bytes(s);
+  switch (s.threads) {
+    case 128: return launch_persistent(k_write<S, 128>, p, 128, smem, num_sms, s.grid, stream);
+    case 256: return launch_persistent(k_write<S, 256>, p, 256, smem, num_sms, s.grid, stream);
+    case 512: return launch_persistent(k_write<S, 512>, p, 512, smem, num_sms, s.grid, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
 
 size_t two_phase_smem_bytes(const LaunchShape& s) {
@@ -282,6 +295,17 @@ cudaError_t launch_decode_two_phase(const DecodeParams& p, const LaunchShape& s,
     case 128: return launch_s<128>(p, s, num_sms, stream);
     case 256: return launch_s<256>(p, s, num_sms, stream);
     case 512: return launch_s<512>(p, s, num_sms, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_write(const DecodeParams& p, const LaunchShape& s, int num_sms,
+                         cudaStream_t stream) {
+  if (p.long_cap != s.long_cap || p.window != s.window || s.window < s.S) return cudaErrorInvalidValue;
+  switch (s.S) {
+    case 64: return launch_write_s<64>(p, s, num_sms, stream);
+    case 128: return launch_write_s<128>(p, s, num_sms, stream);
+    case 256: return launch_write_s<256>(p, s, num_sms, stream);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -40,6 +40,22 @@ size_t two_phase_smem_bytes(const LaunchShape& s);
 // Bytes per stored codeword count for subsequences of S bits.
 size_t count_bytes_per_subsequence(uint32_t S);
 
+// Decode-and-write kernel alone, for fields whose counts and gap entries are
+// already in place (self-synchronisation writes them).
+cudaError_t launch_write(const DecodeParams& p, const LaunchShape& s, int num_sms,
+                         cudaStream_t stream);
+
+// Self-synchronisation (Sec. III-B, IV-A) without waiting between tiles: the
+// synchronising kernel guesses each tile's first start and writes per-
+// subsequence starts (F.gap_out) and codeword counts, tile totals and tile
+// links; a one-block-per-field kernel then re-synchronises, in order, the
+// tiles whose guess was wrong.
+cudaError_t launch_sync(const DecodeParams& p, const LaunchShape& s, int num_sms,
+                        cudaStream_t stream);
+
+// Dynamic shared memory of the synchronising kernels.
+size_t sync_smem_bytes(const LaunchShape& s);
+
 // Decodes all fields of `p` with the gap-array variant (Sec. III-C) or the
 // self-synchronising variant (Sec. III-B, IV-A); with p.sync_only the latter
 // writes the gap arrays instead of decoding.

@@ -1,0 +1,404 @@
+// sync.cu -- self-synchronisation (Sec. III-B, with the early exit of
+// Sec. IV-A): finds the first codeword of every subsequence from the bitstream
+// alone, and counts the codewords of each subsequence on the way.
+//
+//   k_sync  one tile (B subsequences of S bits) per block pass, no waiting on
+//           other tiles.  A few lanes first re-synchronise the subsequences
+//           just before the tile to guess where its first codeword starts.
+//           Every thread then decodes its subsequence without writing from the
+//           nominal start i*S and stops past the subsequence end.  In rounds,
+//           a thread whose start differs from its predecessor's stop position
+//           walks the new and the old path side by side until they meet at a
+//           common codeword boundary -- from there on both coincide, so the old
+//           stop and count stay valid.  Rounds end when no start changes.
+//           The kernel writes each subsequence's start (as a gap entry) and
+//           codeword count, the tile's count, and the tile's assumed start and
+//           final stop offsets.
+//   k_fix   one block per field checks, in order, that every tile's assumed
+//           start equals its predecessor's stop; a tile where it does not (the
+//           guess was wrong) is synchronised again from the true start, which
+//           may change its stop and so the next check.  With Huffman codes
+//           this is rare, but streams that never re-synchronise (e.g. equal
+//           length codes) are fixed tile by tile and still come out right.
+//
+// The gap entries and counts then feed the decode-and-write kernel.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "decode_common.cuh"
+#include "kernels.h"
+
+namespace hd {
+namespace {
+
+using namespace dev;
+
+constexpr int kSegTiles = 256;
+
+template <int S>
+struct CountT {
+  using T = uint8_t;
+};
+template <>
+struct CountT<256> {
+  using T = uint16_t;
+};
+
+template <int S>
+__host__ __device__ constexpr int presync_lanes() {
+  return 1024 / S < 32 ? 1024 / S : 32;
+}
+
+// Decodes codewords (lengths only) from p while p < end; returns the stop.
+template <int STRIDE>
+__device__ __forceinline__ uint32_t walk(const Tables& T, const uint32_t* col, uint32_t p,
+                                         uint32_t end, uint32_t& c) {
+  bool bad = false;
+  while (p < end) {
+    p += code_len(T, peek<STRIDE>(col, p), bad);
+    ++c;
+  }
+  return p;
+}
+
+// Replaces the path from s (stop e, count c) by the path from ns: the two are
+// walked side by side until they share a codeword boundary.
+template <int STRIDE>
+__device__ __forceinline__ void repath(const Tables& T, const uint32_t* col, uint32_t end,
+                                       uint32_t ns, uint32_t& s, uint32_t& e, uint32_t& c) {
+  uint32_t a = ns, b = s, ca = 0, cb = 0;
+  bool met = false, bad = false;
+  for (;;) {
+    if (a == b) {
+      met = true;
+      break;
+    }
+    if (a >= end && b >= end) break;
+    if (a < b) {
+      a += code_len(T, peek<STRIDE>(col, a), bad);
+      ++ca;
+    } else {
+      b += code_len(T, peek<STRIDE>(col, b), bad);
+      ++cb;
+    }
+  }
+  if (met) {
+    c = ca + (c - cb);
+  } else {
+    c = ca;
+    e = a;
+  }
+  s = ns;
+}
+
+// Synchronisation rounds over one tile (every thread of the block calls it).
+// Thread 0's predecessor stopped at e_pred (thread 0 starts at e_pred - S).
+// Returns false if the round cap was hit.
+template <int S, int B>
+__device__ __forceinline__ bool sync_rounds(const Tables& T, const uint32_t* col, bool valid,
+                                            uint32_t end, uint32_t e_pred, uint32_t& s,
+                                            uint32_t& e, uint32_t& c, uint32_t* s_e_last) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  for (uint32_t round = 0;; ++round) {
+    uint32_t e_prev = __shfl_up_sync(0xffffffffu, e, 1);
+    if (lane == 31) s_e_last[warp] = e;
+    __syncthreads();
+    if (lane == 0) e_prev = warp ? s_e_last[warp - 1] : e_pred;
+    bool changed = false;
+    uint32_t ns = s;
+    if (valid) {
+      ns = e_prev - S;
+      changed = ns != s;
+    }
+    if (!__syncthreads_or(changed)) return true;
+    if (round > B + 1) return false;
+    if (changed) repath<B>(T, col, end, ns, s, e, c);
+  }
+}
+
+// Lanes 0..PRE-1 of warp 0 guess where the tile starting at subsequence i0
+// begins by self-synchronising the PRE subsequences before it.
+template <int S, int PRE>
+__device__ __forceinline__ uint32_t presync_guess(const Tables& T, uint32_t* s_pre,
+                                                  const FieldDesc& F, uint64_t i0) {
+  const int lane = threadIdx.x & 31;
+  const bool on = lane < PRE;
+  uint32_t* col = s_pre + lane;
+  if (on) stage_units<S>(col, F, i0 - PRE + lane, PRE);
+  __syncwarp();
+  uint32_t s = 0, e = 0, c = 0;
+  if (on) e = walk<PRE>(T, col, 0, S, c);
+  for (int round = 0; round < PRE + 2; ++round) {
+    const uint32_t e_prev = __shfl_up_sync(0xffffffffu, e, 1);
+    const uint32_t ns = (on && lane) ? e_prev - S : s;
+    const bool changed = ns != s;
+    if (!__any_sync(0xffffffffu, changed)) break;
+    if (changed) repath<PRE>(T, col, S, ns, s, e, c);
+  }
+  return __shfl_sync(0xffffffffu, e, PRE - 1) - S;
+}
+
+template <int B>
+__device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* s_warp) {
+  constexpr int NW = B / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) s_warp[warp] = v;
+  __syncthreads();
+  uint32_t tot = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) tot += s_warp[w];
+  __syncthreads();
+  return tot;
+}
+
+struct SyncShared {
+  uint32_t* s_warp;
+  uint32_t* s_e_last;
+  uint32_t* s_x;  // [2]: broadcast slots
+};
+
+// Synchronises tile tl of field F given its first start a0 (or, when guess is
+// set, a guessed one), writes the tile's gap entries, counts and totals, and
+// returns the start it used.  tile_flag[g] records whether the field's last
+// subsequence ran past nbits; hitting the round cap sets kErrNoSync.
+template <int S, int B>
+__device__ __forceinline__ uint32_t sync_tile(const DecodeParams& P, const FieldDesc& F,
+                                              const Tables& T, bool table_ok, uint64_t g,
+                                              bool guess, uint32_t a0, uint32_t* s_bits,
+                                              uint32_t* s_pre, const SyncShared& sh,
+                                              bool fix) {
+  using CT = typename CountT<S>::T;
+  constexpr int PRE = presync_lanes<S>();
+  const int t = threadIdx.x, warp = t >> 5;
+  uint32_t* col = s_bits + t;
+  const uint64_t tl = g - F.unit_begin;
+  const uint64_t i = tl * B + t;
+  const bool valid = table_ok && i < F.nsub;
+  uint32_t end = 0;
+  if (valid) {
+    stage_units<S>(col, F, i, B);
+    const uint64_t rem = F.nbits - i * S;
+    end = rem < S ? static_cast<uint32_t>(rem) : S;
+  }
+  if (guess && warp == 0) {
+    const uint32_t gs = (tl > 0 && table_ok) ? presync_guess<S, PRE>(T, s_pre, F, tl * B) : 0u;
+    if (t == 0) sh.s_x[0] = gs;
+  }
+  uint32_t s = 0, e = 0, c = 0;
+  if (valid) e = walk<B>(T, col, 0, end, c);
+  __syncthreads();
+  if (guess) a0 = sh.s_x[0];
+  uint32_t flags = 0;
+  if (!sync_rounds<S, B>(T, col, valid, end, S + a0, s, e, c, sh.s_e_last)) flags |= 2u;
+  if (valid && i + 1 == F.nsub && e != end) flags |= 1u;
+  if (valid) {
+    F.gap_out[i] = static_cast<uint8_t>(s);
+    reinterpret_cast<CT*>(P.counts)[F.count_begin + i] = static_cast<CT>(c);
+  }
+  if (t == B - 1) sh.s_x[1] = e - S;
+  if (t == 0 && (flags & 2u)) atomicOr(F.err, kErrNoSync);
+  const bool overran = __syncthreads_or(flags & 1u) != 0;
+  const uint32_t C = block_sum<B>(c, sh.s_warp);
+  if (t == 0) {
+    const uint32_t oldC = fix ? P.tile_total[g] : 0u;
+    P.tile_total[g] = C;
+    atomicAdd(reinterpret_cast<unsigned long long*>(P.seg_total + g / kSegTiles),
+              static_cast<unsigned long long>(C) - static_cast<unsigned long long>(oldC));
+    P.tile_a[g] = static_cast<uint8_t>(a0);
+    P.tile_e[g + 1] = static_cast<uint8_t>(sh.s_x[1]);
+    P.tile_flag[g] = overran ? 1u : 0u;
+  }
+  __syncthreads();
+  return a0;
+}
+
+template <int S, int B>
+__global__ void __launch_bounds__(B) k_sync(const __grid_constant__ DecodeParams P) {
+  constexpr int W = S / 32 + 1;
+  constexpr int PRE = presync_lanes<S>();
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* s_lut = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* s_bits = s_lut + (1u << P.K);
+  uint32_t* s_pre = s_bits + W * B;
+  uint16_t* s_long = reinterpret_cast<uint16_t*>(s_pre + W * PRE);
+  __shared__ uint64_t s_end[34];
+  __shared__ uint32_t s_base[34];
+  __shared__ uint32_t s_meta[3];
+  __shared__ uint32_t s_warp[B / 32];
+  __shared__ uint32_t s_e_last[B / 32];
+  __shared__ uint32_t s_x[2];
+  const SyncShared sh{s_warp, s_e_last, s_x};
+
+  uint32_t cur_field = 0xffffffffu;
+  for (uint64_t g = blockIdx.x; g < P.total_units; g += gridDim.x) {
+    const uint32_t fi = find_field(P, g);
+    const FieldDesc& F = field_of(P, fi);
+    if (fi != cur_field) {
+      __syncthreads();
+      load_table(F.table, P.K, s_lut, s_end, s_base, s_meta, B, s_long, P.long_cap);
+      cur_field = fi;
+      __syncthreads();
+    }
+    const Tables T{s_lut,
+                   s_end,
+                   s_base,
+                   reinterpret_cast<const uint16_t*>(reinterpret_cast<const char*>(F.table) +
+                                                     kTableHeaderBytes + (4u << P.K)),
+                   s_long,
+                   s_meta[2],
+                   P.long_cap,
+                   s_meta[0],
+                   32u - P.K};
+    sync_tile<S, B>(P, F, T, s_meta[1] == 0, g, true, 0u, s_bits, s_pre, sh, false);
+  }
+}
+
+// Smallest tile g in [lo, g1) whose assumed start differs from where its
+// predecessor stopped (tile_a[g] != tile_e[g]), or g1.  Reads both arrays as
+// 16-byte vectors, B * 16 tiles per round, and stops at the first round that
+// finds one.  All threads of the block call it.
+template <int B>
+__device__ __forceinline__ uint64_t first_broken(const DecodeParams& P, uint64_t lo, uint64_t g1,
+                                                 unsigned long long* s_first) {
+  const int t = threadIdx.x;
+  if (t == 0) *s_first = g1;
+  __syncthreads();
+  const uint64_t q_end = (g1 + 15) / 16;
+  for (uint64_t q0 = lo / 16; q0 < q_end; q0 += B) {
+    const uint64_t q = q0 + t;
+    uint64_t found = g1;
+    if (q < q_end) {
+      const uint4 a = *reinterpret_cast<const uint4*>(P.tile_a + 16 * q);
+      const uint4 e = *reinterpret_cast<const uint4*>(P.tile_e + 16 * q);
+      const uint32_t x[4] = {a.x ^ e.x, a.y ^ e.y, a.z ^ e.z, a.w ^ e.w};
+#pragma unroll
+      for (int k = 3; k >= 0; --k) {
+#pragma unroll
+        for (int j = 3; j >= 0; --j) {
+          const uint64_t g = 16 * q + 4 * k + j;
+          if (((x[k] >> (8 * j)) & 0xFFu) && g >= lo && g < g1) found = g;
+        }
+      }
+      if (found < g1) atomicMin(s_first, static_cast<unsigned long long>(found));
+    }
+    if (__syncthreads_or(found < g1)) break;
+  }
+  const uint64_t f = *s_first;
+  __syncthreads();
+  return f;
+}
+
+// One block per field: finds, in order, every tile whose assumed start is not
+// where its predecessor stopped and synchronises it again from the true start
+// (which can move its own stop, so the scan resumes right after it); then
+// checks that the field's last subsequence ended at nbits.
+template <int S, int B>
+__global__ void __launch_bounds__(B) k_fix(const __grid_constant__ DecodeParams P) {
+  constexpr int W = S / 32 + 1;
+  constexpr int PRE = presync_lanes<S>();
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* s_lut = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* s_bits = s_lut + (1u << P.K);
+  uint32_t* s_pre = s_bits + W * B;
+  uint16_t* s_long = reinterpret_cast<uint16_t*>(s_pre + W * PRE);
+  __shared__ uint64_t s_end[34];
+  __shared__ uint32_t s_base[34];
+  __shared__ uint32_t s_meta[3];
+  __shared__ uint32_t s_warp[B / 32];
+  __shared__ uint32_t s_e_last[B / 32];
+  __shared__ uint32_t s_x[2];
+  __shared__ unsigned long long s_first;
+  const SyncShared sh{s_warp, s_e_last, s_x};
+
+  const uint32_t fi = blockIdx.x;
+  if (fi >= P.nfields) return;
+  const FieldDesc& F = field_of(P, fi);
+  if (F.nunits == 0) return;
+  load_table(F.table, P.K, s_lut, s_end, s_base, s_meta, B, s_long, P.long_cap);
+  __syncthreads();
+  const Tables T{s_lut,
+                 s_end,
+                 s_base,
+                 reinterpret_cast<const uint16_t*>(reinterpret_cast<const char*>(F.table) +
+                                                   kTableHeaderBytes + (4u << P.K)),
+                 s_long,
+                 s_meta[2],
+                 P.long_cap,
+                 s_meta[0],
+                 32u - P.K};
+  const bool table_ok = s_meta[1] == 0;
+  const uint64_t g0 = F.unit_begin, g1 = F.unit_begin + F.nunits;
+  uint64_t cursor = g0 + 1;
+  while (table_ok && cursor < g1) {
+    const uint64_t gb = first_broken<B>(P, cursor, g1, &s_first);
+    if (gb >= g1) break;
+    sync_tile<S, B>(P, F, T, table_ok, gb, false, P.tile_e[gb], s_bits, s_pre, sh, true);
+    cursor = gb + 1;
+  }
+  if (threadIdx.x == 0) {
+    if (!table_ok) atomicOr(F.err, kErrTable);
+    else if (P.tile_flag[g1 - 1]) atomicOr(F.err, kErrCode);
+  }
+}
+
+template <int S, int B>
+cudaError_t launch_sb(const DecodeParams& p, const LaunchShape& s, int num_sms,
+                      cudaStream_t stream) {
+  const size_t smem = sync_smem_bytes(s);
+  auto ks = k_sync<S, B>;
+  auto kf = k_fix<S, B>;
+  cudaError_t e =
+      cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks, B, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  uint64_t grid = static_cast<uint64_t>(per_sm) * num_sms;
+  if (s.grid && s.grid < grid) grid = s.grid;
+  if (grid > p.total_units) grid = p.total_units;
+  if (grid == 0) return cudaSuccess;
+  ks<<<static_cast<unsigned>(grid), B, smem, stream>>>(p);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  kf<<<p.nfields, B, smem, stream>>>(p);
+  return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_s(const DecodeParams& p, const LaunchShape& s, int num_sms,
+                     cudaStream_t stream) {
+  switch (s.threads) {
+    case 128: return launch_sb<S, 128>(p, s, num_sms, stream);
+    case 256: return launch_sb<S, 256>(p, s, num_sms, stream);
+    case 512: return launch_sb<S, 512>(p, s, num_sms, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+size_t sync_smem_bytes(const LaunchShape& s) {
+  const size_t W = s.S / 32 + 1;
+  const size_t pre = 1024 / s.S < 32 ? 1024 / s.S : 32;
+  size_t b = (static_cast<size_t>(1) << s.K) * 4 + W * s.threads * 4 + W * pre * 4;
+  b += static_cast<size_t>(s.long_cap) * 2;
+  return (b + 15) & ~static_cast<size_t>(15);
+}
+
+cudaError_t launch_sync(const DecodeParams& p, const LaunchShape& s, int num_sms,
+                        cudaStream_t stream) {
+  if (p.long_cap != s.long_cap) return cudaErrorInvalidValue;
+  switch (s.S) {
+    case 64: return launch_s<64>(p, s, num_sms, stream);
+    case 128: return launch_s<128>(p, s, num_sms, stream);
+    case 256: return launch_s<256>(p, s, num_sms, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace hd

@@ -223,17 +223,27 @@ def test_corrupt_streams(ctx, with_gap):
         assert st in (hd.HD_OK, hd.HD_ERR_CORRUPT)
         assert np.all(res[cc["n"]:] == np.uint16(CANARY))
     if with_gap:
+        # entries at multiples of 4 are read by every decoder subsequence size
+        # (128 to 512 bits over a 128-bit stream): a wrong one must be caught
+        for k, bad in ((4 * (len(c["gap"]) // 8), lambda v: 200),
+                       (4 * (len(c["gap"]) // 12), lambda v: v ^ 1)):
+            cc = dict(c)
+            g = c["gap"].copy()
+            g[k] = bad(int(g[k]))
+            cc["gap"] = g
+            st, res = run_decode(ctx, cc, True)
+            assert st == hd.HD_ERR_CORRUPT
+            assert np.all(res[cc["n"]:] == np.uint16(CANARY))
+        # an entry a wider decoder subsequence skips: caught, or not needed
         cc = dict(c)
         g = c["gap"].copy()
-        g[len(g) // 2] = 200
+        g[4 * (len(g) // 8) + 1] ^= 1
         cc["gap"] = g
         st, res = run_decode(ctx, cc, True)
-        assert st == hd.HD_ERR_CORRUPT
-        g = c["gap"].copy()
-        g[len(g) // 3] ^= 1
-        cc["gap"] = g
-        st, res = run_decode(ctx, cc, True)
-        assert st == hd.HD_ERR_CORRUPT
+        if st == hd.HD_OK:
+            assert np.array_equal(res[:c["n"]], expect(c))
+        else:
+            assert st == hd.HD_ERR_CORRUPT
 
 
 def test_invalid_codebook_and_arguments(ctx):
