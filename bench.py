@@ -222,9 +222,9 @@ def run_gpu(args):
     out = torch.empty(n, dtype=torch.int16, device=f"cuda:{dev}")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
     ctx = hd.Context(dev)
-    if args.threads or args.window or args.lut_bits or args.scratch_syms or args.subseq_bits:
+    if args.threads or args.window or args.lut_bits or args.subseq_bits:
         ctx.set_config(subseq_bits=args.subseq_bits, threads=args.threads, window=args.window,
-                       lut_bits=args.lut_bits, scratch_syms=args.scratch_syms)
+                       lut_bits=args.lut_bits)
     stream = torch.cuda.current_stream()
 
     # correctness of the timed configuration (round trip against the codes)
@@ -355,9 +355,9 @@ def run_profile_case(args):
     f = hd.DeviceField.upload(enc, lengths, n, with_gap=args.profile_strategy == "gap")
     out = torch.empty(n, dtype=torch.int16, device="cuda")
     ctx = hd.Context(0)
-    if args.threads or args.window or args.lut_bits or args.scratch_syms or args.subseq_bits:
+    if args.threads or args.window or args.lut_bits or args.subseq_bits:
         ctx.set_config(subseq_bits=args.subseq_bits, threads=args.threads, window=args.window,
-                       lut_bits=args.lut_bits, scratch_syms=args.scratch_syms)
+                       lut_bits=args.lut_bits)
     for _ in range(args.warmup):
         ctx.decode(f, out)
     torch.cuda.synchronize()
@@ -383,7 +383,6 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--window", type=int, default=0)
     ap.add_argument("--lut-bits", dest="lut_bits", type=int, default=0)
-    ap.add_argument("--scratch-syms", dest="scratch_syms", type=int, default=0)
     ap.add_argument("--subseq-bits", dest="subseq_bits", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-strategy", choices=["gap", "selfsync"], default=None,

@@ -55,7 +55,7 @@ extern "C" {
 #define HD_ERR_SYMBOL (-3)  /* input symbol outside the alphabet or without code */
 #define HD_ERR_CORRUPT (-4) /* stream is no valid encoding of n symbols */
 #define HD_ERR_NOSYNC (-5)  /* self-synchronisation did not converge in its cap */
-#define HD_ERR_TIMEOUT (-6) /* a device-side wait gave up (look-back chain) */
+#define HD_ERR_TIMEOUT (-6) /* a device-side wait gave up (hd_decode_static) */
 #define HD_ERR_CUDA (-7)    /* a CUDA runtime call failed */
 #define HD_ERR_NOMEM (-8)   /* host or device allocation failed / over budget */
 #define HD_ERR_BUSY (-9)    /* serve: queue full or server stopped */
@@ -92,8 +92,9 @@ int hd_encode(const uint16_t* codes, uint64_t n, const uint8_t* lengths, uint32_
 typedef struct hd_ctx hd_ctx;
 
 /* Creates a context bound to CUDA device `device`.  The context owns its
- * device workspace (look-back states, decode tables, error words), which grows
- * on demand with cudaMalloc outside of any decode call's device work. */
+ * device workspace (decode tables, per-subsequence codeword counts and
+ * starts, per-tile totals, error words), which grows on demand with
+ * cudaMalloc outside of any decode call's device work. */
 int hd_ctx_create(int device, hd_ctx** out);
 int hd_ctx_destroy(hd_ctx* ctx);
 
@@ -112,14 +113,14 @@ typedef struct hd_field {
 
 /* Launch shape (0 = library default / autotuned choice). */
 typedef struct hd_config {
-  uint32_t subseq_bits; /* decoder subsequence: a multiple of the field's S, <= 256 */
+  uint32_t subseq_bits; /* decoder subsequence bits.  Gap-array decode: a multiple
+                           of the field's S, <= 512 (0 = max(256, S));
+                           self-synchronisation: 64, 128 or 256 (512 acts as
+                           256; 0 = the field's S) */
   uint32_t threads;     /* threads per block = subsequences per tile: 128, 256, 512 */
   uint32_t window;      /* shared-memory output window in symbols (Alg. 1 buffer);
                            0 = sized from the field's mean code length */
   uint32_t lut_bits;    /* first-level decode-table index bits, 8 .. 13 */
-  uint32_t scratch_syms; /* self-synchronising decode: decoded symbols each thread
-                           keeps in shared memory (a multiple of 8, <= S);
-                           threads with more codewords decode them again */
 } hd_config;
 
 /* Sets the launch shape used by later decodes on this context (NULL resets to
@@ -138,7 +139,8 @@ int hd_decode(hd_ctx* ctx, const hd_field* f, uint16_t* d_out, void* stream);
 
 /* Waits for `stream` and returns the status of the last hd_decode /
  * hd_sync_points / hd_decode_batch queued on this context: HD_OK,
- * HD_ERR_CORRUPT, HD_ERR_NOSYNC, HD_ERR_TIMEOUT or HD_ERR_CUDA. */
+ * HD_ERR_CORRUPT (stream, gap array or n inconsistent), HD_ERR_ARG (length
+ * table with Kraft sum > 1 or a length > 32), HD_ERR_NOSYNC or HD_ERR_CUDA. */
 int hd_status(hd_ctx* ctx, void* stream);
 
 /* Self-synchronisation only (Sec. III-B2 steps 1-2): computes the gap array
@@ -147,9 +149,9 @@ int hd_status(hd_ctx* ctx, void* stream);
  * via hd_status. */
 int hd_sync_points(hd_ctx* ctx, const hd_field* f, uint8_t* gap_out, void* stream);
 
-/* Decodes nf independent fields (device pointers, own codebooks) in one
- * persistent launch; d_outs[i] receives field i.  Per-field status via
- * hd_batch_status. */
+/* Decodes nf independent fields (device pointers, own codebooks) with one
+ * launch sequence for all gap-array fields and one for all self-synchronising
+ * fields; d_outs[i] receives field i.  Per-field status via hd_batch_status. */
 int hd_decode_batch(hd_ctx* ctx, const hd_field* fs, uint32_t nf, uint16_t* const* d_outs,
                     void* stream);
 /* Waits for `stream`; status[i] = status of field i of the last batch. Returns

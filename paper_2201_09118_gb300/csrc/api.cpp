@@ -1,6 +1,6 @@
 // api.cpp -- the C ABI of hd.h: context, argument checks, workspace layout
-// and the launch sequence (decode-table kernel, then one persistent decode
-// kernel).
+// and the launch sequence (decode-table kernel, then the decode kernels of
+// the field's strategy).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,7 +44,6 @@ using hd::FieldDesc;
 
 constexpr uint32_t kDefaultThreads = 256;
 constexpr uint32_t kDefaultK = 12;
-constexpr uint64_t kTimeoutCycles = 4000000000ull;  // ~2 s at GB300 clocks
 
 struct DeviceGuard {
   int prev = -1;
@@ -134,7 +133,6 @@ hd::LaunchShape shape_for(const hd_ctx* c, uint32_t stream_S, bool gap) {
   s.threads = c->cfg.threads ? c->cfg.threads : kDefaultThreads;
   s.K = c->cfg.lut_bits ? c->cfg.lut_bits : kDefaultK;
   s.window = c->cfg.window;  // 0: chosen per launch
-  s.cmax = c->cfg.scratch_syms;  // 0: chosen per launch
   s.grid = 0;
   return s;
 }
@@ -191,7 +189,6 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
     s.window = static_cast<uint32_t>(std::min(std::max(want, 1024.0), 16384.0));
   }
   s.window = static_cast<uint32_t>(align_up(std::max(s.window, s.S), 8));
-  s.cmax = 0;
   {
     // the window is an optimisation (larger outputs go through several
     // windows), so it shrinks to fit shared memory
@@ -211,8 +208,6 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
   }
   // workspace layout; [0, zero_bytes) is cleared by the table kernel
   size_t off = 0;
-  const size_t ctrl_off = off;  // ticket, abort flag
-  off += 16;
   const size_t err_off = off;
   off = align_up(off + 4ull * nf, 16);
   const size_t seg_off = off;  // codewords per 256 tiles
@@ -262,7 +257,7 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
   pp.fields = reinterpret_cast<const FieldDesc*>(ws + desc_off);
   pp.nfields = nf;
   pp.K = s.K;
-  pp.zero_ptr = reinterpret_cast<uint4*>(ws + ctrl_off);
+  pp.zero_ptr = reinterpret_cast<uint4*>(ws);
   pp.zero_vec = zero_bytes / 16;
   pp.zero_blocks = static_cast<uint32_t>(std::min<uint64_t>((pp.zero_vec + 4095) / 4096, 64));
   if (pp.zero_blocks == 0) pp.zero_blocks = 1;
@@ -276,13 +271,8 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
   dp.nfields = nf;
   dp.K = s.K;
   dp.window = s.window;
-  dp.sync_only = sync_only ? 1u : 0u;
-  dp.cmax = s.cmax;
   dp.long_cap = s.long_cap;
   dp.total_units = total_tiles;
-  dp.ticket = reinterpret_cast<uint32_t*>(ws + ctrl_off);
-  dp.abort_flag = reinterpret_cast<uint32_t*>(ws + ctrl_off) + 1;
-  dp.timeout_cycles = kTimeoutCycles;
   dp.counts = ws + count_off;
   dp.tile_total = reinterpret_cast<uint32_t*>(ws + tile_off);
   dp.seg_total = reinterpret_cast<uint64_t*>(ws + seg_off);
@@ -383,7 +373,6 @@ int hd_set_config(hd_ctx* c, const hd_config* cfg) {
     return HD_ERR_ARG;
   if (cfg->lut_bits && (cfg->lut_bits < 8 || cfg->lut_bits > 13)) return HD_ERR_ARG;
   if (cfg->window && (cfg->window < 64 || cfg->window > 32768)) return HD_ERR_ARG;
-  if (cfg->scratch_syms && (cfg->scratch_syms % 8 || cfg->scratch_syms > 256)) return HD_ERR_ARG;
   c->cfg = *cfg;
   return HD_OK;
 }
@@ -395,7 +384,6 @@ int hd_get_config(hd_ctx* c, hd_config* cfg) {
   cfg->threads = c->cfg.threads ? c->cfg.threads : kDefaultThreads;
   cfg->window = c->cfg.window ? c->cfg.window : c->last_shape.window;
   cfg->lut_bits = c->cfg.lut_bits ? c->cfg.lut_bits : kDefaultK;
-  cfg->scratch_syms = c->cfg.scratch_syms;
   return HD_OK;
 }
 

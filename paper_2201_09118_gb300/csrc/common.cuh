@@ -52,7 +52,7 @@ struct FieldDesc {
   uint64_t unit_begin;     // index of this field's first tile in the launch
   uint64_t nunits;         // tiles of this field
   uint32_t* err;           // error bits of this field
-  uint8_t* gap_out;        // sync-point mode: gap array written here
+  uint8_t* gap_out;        // self-synchronisation: subsequence starts written here
   uint64_t count_begin;    // first entry of this field's per-subsequence counts
 };
 
@@ -72,7 +72,6 @@ struct DecodeParams {
   uint32_t nfields;
   uint32_t K;               // first-level table bits for this launch
   uint32_t window;          // shared-memory output window, symbols (Alg. 1 buffer)
-  uint32_t sync_only;       // 1: write gap arrays, do not decode
   uint32_t cmax;            // scratch symbols per subsequence (<= S)
   uint32_t long_cap;        // sorted symbols of long codes kept in shared memory
   uint64_t total_units;     // tiles in the launch

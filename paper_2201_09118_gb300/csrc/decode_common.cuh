@@ -1,6 +1,6 @@
 // decode_common.cuh -- device building blocks of the decode kernels:
-// bitstream staging, decode-table lookups, block scans, the decoupled
-// look-back over tiles and the shared-memory staged output window.
+// bitstream staging, decode-table lookups, block scans, bounded waits and the
+// shared-memory staged output window.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,12 +26,6 @@ __device__ __forceinline__ uint32_t ld_relaxed32(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
-}
-
-__device__ __forceinline__ uint64_t now_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
 }
 
 __device__ __forceinline__ uint4 ldg_v4(const uint32_t* p) {
@@ -147,49 +141,6 @@ __device__ __forceinline__ bool backoff_wait(const DecodeParams& P, uint64_t t0)
     return false;
   }
   return true;
-}
-
-// Decoupled look-back over the work units of one field (warp 0 only).
-// Publishes this unit's count as an aggregate, sums predecessors' aggregates
-// back to the nearest inclusive prefix, then publishes its own inclusive
-// prefix.  Returns the exclusive prefix (the unit's first output index).
-__device__ __forceinline__ uint64_t lookback_counts(const DecodeParams& P, uint64_t g,
-                                                    uint64_t first_unit, uint64_t C,
-                                                    uint32_t* err) {
-  const int lane = threadIdx.x & 31;
-  uint64_t* st = P.unit_state;
-  if (g == first_unit) {
-    if (lane == 0) st_relaxed(st + g, kStateInc | C);
-    return 0;
-  }
-  if (lane == 0) st_relaxed(st + g, kStateAgg | C);
-  uint64_t excl = 0;
-  int64_t j = static_cast<int64_t>(g) - 1;
-  const int64_t lo = static_cast<int64_t>(first_unit);
-  const uint64_t t0 = static_cast<uint64_t>(clock64());
-  for (;;) {
-    const int64_t idx = j - lane;
-    const uint64_t s = idx >= lo ? ld_relaxed(st + idx) : kStateInc;
-    const uint32_t flag = static_cast<uint32_t>(s >> 62);
-    const uint32_t inc = __ballot_sync(0xffffffffu, flag == 2u);
-    const uint32_t notready = __ballot_sync(0xffffffffu, flag == 0u);
-    const uint32_t need = inc ? (((inc & (0u - inc)) << 1) - 1u) : 0xffffffffu;
-    if (notready & need) {
-      bool go = true;
-      if (lane == 0) go = backoff_wait(P, t0);
-      go = __shfl_sync(0xffffffffu, go, 0);
-      if (!go) {
-        if (lane == 0) atomicOr(err, kErrTimeout);
-        break;
-      }
-      continue;
-    }
-    excl += warp_sum_u64((need >> lane) & 1u ? (s & kStateValMask) : 0ull);
-    if (inc) break;
-    j -= 32;
-  }
-  if (lane == 0) st_relaxed(st + g, kStateInc | ((excl + C) & kStateValMask));
-  return excl;
 }
 
 // Algorithm 1 (Sec. IV-B): the block's output [0, C) is produced through a

@@ -27,8 +27,8 @@ struct LaunchShape {
   uint32_t grid;     // persistent blocks (0: full occupancy)
 };
 
-// Dynamic shared memory one decode block needs for a launch shape.
-size_t decode_smem_bytes(const LaunchShape& s, bool self_sync);
+// Dynamic shared memory of the single-pass gap-array kernel.
+size_t decode_smem_bytes(const LaunchShape& s);
 
 // Two-phase gap-array decode (count kernel, then decode-and-write kernel).
 cudaError_t launch_decode_two_phase(const DecodeParams& p, const LaunchShape& s, int num_sms,
@@ -56,10 +56,11 @@ cudaError_t launch_sync(const DecodeParams& p, const LaunchShape& s, int num_sms
 // Dynamic shared memory of the synchronising kernels.
 size_t sync_smem_bytes(const LaunchShape& s);
 
-// Decodes all fields of `p` with the gap-array variant (Sec. III-C) or the
-// self-synchronising variant (Sec. III-B, IV-A); with p.sync_only the latter
-// writes the gap arrays instead of decoding.
-cudaError_t launch_decode(const DecodeParams& p, const LaunchShape& s, bool self_sync,
-                          int num_sms, cudaStream_t stream);
+// Single-pass gap-array decode (Sec. III-C): one persistent kernel whose
+// tiles take their output offsets from a look-back over per-tile states
+// (p.unit_state, p.ticket, p.abort_flag zeroed before the launch); needs no
+// per-subsequence scratch in global memory.
+cudaError_t launch_decode_single_pass(const DecodeParams& p, const LaunchShape& s, int num_sms,
+                                      cudaStream_t stream);
 
 }  // namespace hd

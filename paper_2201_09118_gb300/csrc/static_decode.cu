@@ -137,7 +137,6 @@ extern "C" int hd_decode_static(const hd_field* f, uint16_t* d_out, void* stream
   dp.nfields = 1;
   dp.K = s.K;
   dp.window = s.window;
-  dp.sync_only = 0;
   dp.cmax = s.cmax;
   dp.long_cap = s.long_cap;
   dp.total_units = units;
@@ -145,7 +144,7 @@ extern "C" int hd_decode_static(const hd_field* f, uint16_t* d_out, void* stream
   dp.ticket = reinterpret_cast<uint32_t*>(scratch);
   dp.abort_flag = reinterpret_cast<uint32_t*>(scratch) + 1;
   dp.timeout_cycles = kTimeoutCycles;
-  if (hd::launch_decode(dp, s, false, num_sms, st) != cudaSuccess) return HD_ERR_CUDA;
+  if (hd::launch_decode_single_pass(dp, s, num_sms, st) != cudaSuccess) return HD_ERR_CUDA;
 
   uint32_t bits = 0;
   if (cudaMemcpyAsync(&bits, scratch + err_off, sizeof(bits), cudaMemcpyDeviceToHost, st) !=

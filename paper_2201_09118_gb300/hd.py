@@ -54,8 +54,7 @@ class hd_field(ctypes.Structure):
 
 class hd_config(ctypes.Structure):
     _fields_ = [("subseq_bits", ctypes.c_uint32), ("threads", ctypes.c_uint32),
-                ("window", ctypes.c_uint32), ("lut_bits", ctypes.c_uint32),
-                ("scratch_syms", ctypes.c_uint32)]
+                ("window", ctypes.c_uint32), ("lut_bits", ctypes.c_uint32)]
 
 
 # every exported symbol of include/hd.h with its ctypes signature
@@ -220,8 +219,8 @@ class Context:
         except Exception:
             pass
 
-    def set_config(self, subseq_bits=0, threads=0, window=0, lut_bits=0, scratch_syms=0):
-        cfg = hd_config(subseq_bits, threads, window, lut_bits, scratch_syms)
+    def set_config(self, subseq_bits=0, threads=0, window=0, lut_bits=0):
+        cfg = hd_config(subseq_bits, threads, window, lut_bits)
         _check("hd_set_config", self._lib.hd_set_config(self.handle, ctypes.byref(cfg)))
 
     def reset_config(self):
@@ -231,7 +230,7 @@ class Context:
         cfg = hd_config()
         _check("hd_get_config", self._lib.hd_get_config(self.handle, ctypes.byref(cfg)))
         return {"subseq_bits": cfg.subseq_bits, "threads": cfg.threads, "window": cfg.window,
-                "lut_bits": cfg.lut_bits, "scratch_syms": cfg.scratch_syms}
+                "lut_bits": cfg.lut_bits}
 
     def decode(self, field: DeviceField, out, stream=None) -> None:
         f = field.c_struct()

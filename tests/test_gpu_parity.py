@@ -95,9 +95,9 @@ def test_launch_shapes(ctx, S, threads, with_gap):
     x = synth.laplace_codes(200003, scale=30.0, seed=S + threads)
     c = oracle.compress(x, 1024, S=S)
     try:
-        for window, K, cm in ((S, 8, 8), (1024, 11, 16), (0, 12, 0), (8192, 13, S)):
+        for window, K in ((S, 8), (1024, 11), (0, 12), (8192, 13)):
             ctx.set_config(subseq_bits=S, threads=threads, window=max(window, S) if window else 0,
-                           lut_bits=K, scratch_syms=cm)
+                           lut_bits=K)
             check(ctx, c, with_gap)
     finally:
         ctx.reset_config()
