@@ -149,14 +149,43 @@ int hd_status(hd_ctx* ctx, void* stream);
  * via hd_status. */
 int hd_sync_points(hd_ctx* ctx, const hd_field* f, uint8_t* gap_out, void* stream);
 
-/* Decodes nf independent fields (device pointers, own codebooks) with one
- * launch sequence for all gap-array fields and one for all self-synchronising
- * fields; d_outs[i] receives field i.  Per-field status via hd_batch_status. */
+/* Decodes nf independent fields of any sizes (device pointers, own codebooks;
+ * Sec. III-C / III-B per field) with one CUDA graph launch for all gap-array
+ * fields and one for all self-synchronising fields; d_outs[i] receives field
+ * i.  The persistent kernels spread the tiles of all fields over the GPU and
+ * read the batch's sizes from device memory, so a graph captured once per
+ * (strategy, launch shape, power-of-two capacity class) is replayed for every
+ * later batch that fits it.  The launch shape is the context's configuration
+ * when one is set, else the shape hd_autotune chose for the batch's class,
+ * else the defaults.  Asynchronous except that, when both strategies occur,
+ * the call waits for the first group before queuing the second.  Per-field
+ * status via hd_batch_status. */
 int hd_decode_batch(hd_ctx* ctx, const hd_field* fs, uint32_t nf, uint16_t* const* d_outs,
                     void* stream);
 /* Waits for `stream`; status[i] = status of field i of the last batch. Returns
  * the first non-OK status or HD_OK. */
 int hd_batch_status(hd_ctx* ctx, int32_t* status, uint32_t nf, void* stream);
+
+/* Autotuner (launch-configuration choice; the paper tunes the shared-memory
+ * buffer per sequence online, Sec. IV-C, Algorithm 2): decodes the batch with
+ * every candidate shape -- decoder subsequence bits {64, 128, 256, 512} (a
+ * multiple of the largest stream S for gap arrays, at most 256 for
+ * self-synchronisation) x threads {128, 256, 512} x first-level table bits
+ * {11, 12, 13}, window sized from the mean code length -- timing three
+ * replays of each with CUDA events, and keeps the fastest shape that decodes
+ * every field without error.  The choice is stored in the context per batch
+ * class (strategy, mean code length in quarter bits, log2 of the symbol
+ * count, largest stream S) and used by later hd_decode_batch calls of that
+ * class while the context's configuration is all zero.  `best` (may be NULL)
+ * receives the shape chosen for the first strategy group.  Synchronous; the
+ * outputs hold the batch's symbols afterwards.  HD_ERR_CORRUPT if no
+ * candidate decodes the batch cleanly. */
+int hd_autotune(hd_ctx* ctx, const hd_field* fs, uint32_t nf, uint16_t* const* d_outs,
+                void* stream, hd_config* best);
+
+/* Graph statistics of a context: graphs captured since creation and graphs
+ * currently cached. */
+int hd_graph_stats(hd_ctx* ctx, uint64_t* captures, uint32_t* cached);
 
 /* Host-buffer decode: `f` holds HOST pointers (pinned memory is fastest),
  * host_out receives f->n symbols.  Copies the stream, gap array and lengths

@@ -5,13 +5,22 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
 #include "hd.h"
 #include "host_internal.h"
 #include "kernels.h"
+
+// Cached graph: strategy, launch shape, capacities and workspace address.
+using GraphKey = std::tuple<bool, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t,
+                            uint64_t, size_t, uintptr_t>;
+// Autotuner class: strategy, mean code length in quarter bits, log2 of the
+// symbol count, largest stream subsequence size of the batch.
+using TuneKey = std::tuple<bool, uint32_t, uint32_t, uint32_t>;
 
 struct hd_ctx {
   int device = 0;
@@ -36,6 +45,17 @@ struct hd_ctx {
   size_t events_used = 0;
   uint64_t launches = 0;
   hd::LaunchShape last_shape{};  // launch shape of the last decode
+  // graph launches (hd_decode_batch)
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+  cudaStream_t cap_stream = nullptr;  // capture only; graphs run on the caller's stream
+  uint64_t captures = 0;
+  char* pinned = nullptr;             // header + descriptors staged for the copy
+  size_t pinned_cap = 0;
+  cudaEvent_t pinned_ev = nullptr;
+  bool pinned_busy = false;
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};  // autotuner timing
+  // autotuner results: batch class -> launch shape
+  std::map<TuneKey, hd_config> tuned;
 };
 
 namespace {
@@ -68,10 +88,16 @@ int map_err_bits(uint32_t b) {
   return HD_ERR_CORRUPT;
 }
 
+void drop_graphs(hd_ctx* c) {
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+}
+
 int ensure_ws(hd_ctx* c, size_t bytes) {
   if (bytes <= c->ws_cap) return HD_OK;
   if (c->ws) {
     cudaDeviceSynchronize();
+    drop_graphs(c);  // they hold addresses inside the old workspace
     cudaFree(c->ws);
     c->ws = nullptr;
     c->ws_cap = 0;
@@ -165,121 +191,302 @@ void fill_desc(FieldDesc& d, const hd_field* f, const hd::LaunchShape& s, uint16
   d.n = f->n;
 }
 
-// Queues the decode-table build (which also clears the per-launch control
-// region) and the decode kernels for fields that all use the same strategy:
-//   gap array            count kernel, decode-and-write kernel;
-//   self-synchronisation synchronising kernel, link-fix kernel, then the same
-//                        decode-and-write kernel (with sync_only: the first two
-//                        alone, which leave the gap arrays in each gap_out).
-int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape& shape,
-                 bool self_sync, bool sync_only, cudaStream_t st) {
-  const uint32_t nf = static_cast<uint32_t>(descs.size());
+uint64_t pow2_at_least(uint64_t v, uint64_t lo) {
+  uint64_t p = lo;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Workspace layout of one launch; [0, zero) is cleared by the table kernel.
+struct Layout {
+  size_t err = 0, seg = 0, zero = 0, hdr = 0, desc = 0, tab = 0, tile = 0, count = 0;
+  size_t gap = 0, ta = 0, te = 0, tf = 0, total = 0;
+};
+
+Layout make_layout(uint32_t nf, uint64_t tiles, uint64_t subs, size_t tab_bytes,
+                   const hd::LaunchShape& s, bool self_sync, bool own_gap) {
+  Layout L;
+  size_t off = 0;
+  L.err = off;
+  off = align_up(off + 4ull * nf, 16);
+  L.seg = off;  // codewords per 256 tiles
+  off = align_up(off + 8ull * ((tiles + 255) / 256 + 1), 16);
+  L.zero = off;
+  L.hdr = align_up(off, 256);  // launch header, then the field descriptors
+  L.desc = L.hdr + 256;
+  off = L.desc + sizeof(FieldDesc) * nf;
+  L.tab = align_up(off, 256);
+  off = L.tab + tab_bytes;
+  L.tile = align_up(off, 256);
+  off = L.tile + 4ull * tiles;
+  L.count = align_up(off, 256);
+  off = L.count + hd::count_bytes_per_subsequence(s.S) * subs;
+  // self-synchronisation: subsequence starts, tile links (16-byte padded)
+  const size_t link_bytes = align_up(tiles + 1, 16) + 16;
+  L.gap = align_up(off, 256);
+  if (own_gap) off = L.gap + subs;
+  L.ta = align_up(off, 256);
+  L.te = align_up(L.ta + link_bytes, 256);
+  L.tf = align_up(L.te + link_bytes, 256);
+  if (self_sync) off = L.tf + tiles;
+  L.total = align_up(off, 256);
+  return L;
+}
+
+// Host-side preparation of a launch: final shape, per-field tiles, counts
+// and table offsets.
+struct Prepared {
+  hd::LaunchShape s;
+  uint64_t tiles = 0, subs = 0;
+  size_t tab_bytes = 0;
+  std::vector<size_t> tab_off;  // relative to the table region
+};
+
+int prepare_launch(const hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape& shape,
+                   bool self_sync, Prepared& P) {
   hd::LaunchShape s = shape;
-  double bits_per = 0;
+  uint64_t bits = 0, syms = 0;
   uint32_t amax = 0;
   for (auto& d : descs) {
-    bits_per = std::max(bits_per, static_cast<double>(d.nbits) / static_cast<double>(d.n ? d.n : 1));
+    bits += d.nbits;
+    syms += d.n;
     amax = std::max(amax, d.alphabet);
   }
+  const double bits_per = static_cast<double>(bits) / static_cast<double>(syms ? syms : 1);
   // symbols of codes longer than the first-level table, kept in shared memory
   s.long_cap = static_cast<uint32_t>(align_up(std::min<uint32_t>(amax, 4096), 8));
   if (s.window == 0) {
-    // output window: about 1.2x a tile's expected symbol count
+    // output window: about 1.2x a tile's expected symbol count, rounded up to
+    // a multiple of 2048 so that batches of similar code lengths share a shape
     const double want = 1.2 * s.threads * s.S / std::max(bits_per, 0.25) + 64.0;
-    s.window = static_cast<uint32_t>(std::min(std::max(want, 1024.0), 16384.0));
+    s.window = static_cast<uint32_t>(
+        align_up(static_cast<size_t>(std::min(std::max(want, 1024.0), 16384.0)), 2048));
   }
   s.window = static_cast<uint32_t>(align_up(std::max(s.window, s.S), 8));
-  {
-    // the window is an optimisation (larger outputs go through several
-    // windows), so it shrinks to fit shared memory
-    const size_t budget = static_cast<size_t>(c->max_smem) - 2048;
-    while (s.window > std::max<uint32_t>(1024, s.S) && hd::two_phase_smem_bytes(s) > budget)
-      s.window -= 512;
-    if (hd::two_phase_smem_bytes(s) > budget) return HD_ERR_ARG;
-    if (self_sync && hd::sync_smem_bytes(s) > budget) return HD_ERR_ARG;
-  }
-  uint64_t total_tiles = 0, total_sub = 0;
-  for (auto& d : descs) {
-    d.unit_begin = total_tiles;
-    d.nunits = tiles_for(d.nsub, s);
-    total_tiles += d.nunits;
-    d.count_begin = total_sub;
-    total_sub += d.nsub;
-  }
-  // workspace layout; [0, zero_bytes) is cleared by the table kernel
-  size_t off = 0;
-  const size_t err_off = off;
-  off = align_up(off + 4ull * nf, 16);
-  const size_t seg_off = off;  // codewords per 256 tiles
-  off = align_up(off + 8ull * ((total_tiles + 255) / 256 + 1), 16);
-  const size_t zero_bytes = off;
-  off = align_up(off, 256);
-  std::vector<size_t> tab_off(nf);
-  for (uint32_t k = 0; k < nf; ++k) {
-    tab_off[k] = off;
-    off += hd::table_bytes(s.K, descs[k].alphabet);
-  }
-  const size_t desc_off = align_up(off, 256);
-  off = desc_off + (nf > 1 ? sizeof(FieldDesc) * nf : 0);
-  const size_t tile_off = align_up(off, 256);
-  off = tile_off + 4ull * total_tiles;
-  const size_t count_off = align_up(off, 256);
-  off = count_off + hd::count_bytes_per_subsequence(s.S) * total_sub;
-  // self-synchronisation: subsequence starts, tile links (16-byte padded)
-  const size_t link_bytes = align_up(total_tiles + 1, 16) + 16;
-  const size_t gap_off = align_up(off, 256);
-  if (self_sync && !sync_only) off = gap_off + total_sub;
-  const size_t ta_off = align_up(off, 256);
-  const size_t te_off = align_up(ta_off + link_bytes, 256);
-  const size_t tf_off = align_up(te_off + link_bytes, 256);
-  if (self_sync) off = tf_off + total_tiles;
-  int rc = ensure_ws(c, off);
-  if (rc) return rc;
-  char* ws = c->ws;
-  for (uint32_t k = 0; k < nf; ++k) {
+  // the window is an optimisation (larger outputs go through several
+  // windows), so it shrinks to fit shared memory
+  const size_t budget = static_cast<size_t>(c->max_smem) - 2048;
+  while (s.window > std::max<uint32_t>(1024, s.S) && hd::two_phase_smem_bytes(s) > budget)
+    s.window -= 512;
+  if (hd::two_phase_smem_bytes(s) > budget) return HD_ERR_ARG;
+  if (self_sync && hd::sync_smem_bytes(s) > budget) return HD_ERR_ARG;
+  P.s = s;
+  P.tiles = P.subs = 0;
+  P.tab_bytes = 0;
+  P.tab_off.resize(descs.size());
+  for (size_t k = 0; k < descs.size(); ++k) {
     FieldDesc& d = descs[k];
-    d.table = reinterpret_cast<const hd::TableHeader*>(ws + tab_off[k]);
-    d.err = reinterpret_cast<uint32_t*>(ws + err_off) + k;
+    d.unit_begin = P.tiles;
+    d.nunits = tiles_for(d.nsub, s);
+    P.tiles += d.nunits;
+    d.count_begin = P.subs;
+    P.subs += d.nsub;
+    P.tab_off[k] = P.tab_bytes;
+    P.tab_bytes += hd::table_bytes(s.K, d.alphabet);
+  }
+  return HD_OK;
+}
+
+// Points every descriptor at its table, error word and (self-synchronisation)
+// start array inside the workspace.
+void bind_descs(std::vector<FieldDesc>& descs, char* ws, const Layout& L, const Prepared& P,
+                bool self_sync, bool sync_only) {
+  for (size_t k = 0; k < descs.size(); ++k) {
+    FieldDesc& d = descs[k];
+    d.table = reinterpret_cast<const hd::TableHeader*>(ws + L.tab + P.tab_off[k]);
+    d.err = reinterpret_cast<uint32_t*>(ws + L.err) + k;
     if (self_sync) {
-      if (!sync_only) d.gap_out = reinterpret_cast<uint8_t*>(ws + gap_off) + d.count_begin;
+      if (!sync_only) d.gap_out = reinterpret_cast<uint8_t*>(ws + L.gap) + d.count_begin;
       d.gap = d.gap_out;
       d.gap_stride = 1;
     }
   }
-  cudaError_t e = cudaSuccess;
-  if (nf > 1) {
-    e = cudaMemcpyAsync(ws + desc_off, descs.data(), sizeof(FieldDesc) * nf,
-                        cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return HD_ERR_CUDA;
-  }
-  hd::PrepParams pp{};
+}
+
+// Kernel parameters of a launch.  `dyn`: sizes come from the device-side
+// header, the parameters carry the capacities (graph launches).
+void make_params(const std::vector<FieldDesc>& descs, char* ws, const Layout& L,
+                 const hd::LaunchShape& s, bool self_sync, bool dyn, uint32_t nf_param,
+                 uint64_t tiles_param, hd::PrepParams& pp, hd::DecodeParams& dp) {
+  pp = hd::PrepParams{};
   pp.f0 = descs[0];
-  pp.fields = reinterpret_cast<const FieldDesc*>(ws + desc_off);
-  pp.nfields = nf;
+  pp.fields = reinterpret_cast<const FieldDesc*>(ws + L.desc);
+  pp.hdr = dyn ? reinterpret_cast<const hd::LaunchHeader*>(ws + L.hdr) : nullptr;
+  pp.nfields = nf_param;
+  pp.table_blocks = std::min<uint32_t>(nf_param, 1024);
   pp.K = s.K;
   pp.zero_ptr = reinterpret_cast<uint4*>(ws);
-  pp.zero_vec = zero_bytes / 16;
+  pp.zero_vec = L.zero / 16;
   pp.zero_blocks = static_cast<uint32_t>(std::min<uint64_t>((pp.zero_vec + 4095) / 4096, 64));
   if (pp.zero_blocks == 0) pp.zero_blocks = 1;
-  e = hd::launch_prepare(pp, st);
-  if (e != cudaSuccess) return HD_ERR_CUDA;
-  c->launches += 1;
-
-  hd::DecodeParams dp{};
+  dp = hd::DecodeParams{};
   dp.f0 = descs[0];
   dp.fields = pp.fields;
-  dp.nfields = nf;
+  dp.hdr = pp.hdr;
+  dp.nfields = nf_param;
   dp.K = s.K;
   dp.window = s.window;
   dp.long_cap = s.long_cap;
-  dp.total_units = total_tiles;
-  dp.counts = ws + count_off;
-  dp.tile_total = reinterpret_cast<uint32_t*>(ws + tile_off);
-  dp.seg_total = reinterpret_cast<uint64_t*>(ws + seg_off);
+  dp.total_units = tiles_param;
+  dp.counts = ws + L.count;
+  dp.tile_total = reinterpret_cast<uint32_t*>(ws + L.tile);
+  dp.seg_total = reinterpret_cast<uint64_t*>(ws + L.seg);
   if (self_sync) {
-    dp.tile_a = reinterpret_cast<uint8_t*>(ws + ta_off);
-    dp.tile_e = reinterpret_cast<uint8_t*>(ws + te_off);
-    dp.tile_flag = reinterpret_cast<uint8_t*>(ws + tf_off);
+    dp.tile_a = reinterpret_cast<uint8_t*>(ws + L.ta);
+    dp.tile_e = reinterpret_cast<uint8_t*>(ws + L.te);
+    dp.tile_flag = reinterpret_cast<uint8_t*>(ws + L.tf);
+  }
+}
+
+// The kernels of one strategy, in stream order:
+//   gap array            table kernel, count kernel, decode-and-write kernel;
+//   self-synchronisation table kernel, synchronising kernel, link-fix kernel,
+//                        then the same decode-and-write kernel (with sync_only
+//                        the last is left out: the starts stay in each gap_out).
+cudaError_t launch_all(const hd_ctx* c, const hd::PrepParams& pp, const hd::DecodeParams& dp,
+                       const hd::LaunchShape& s, bool self_sync, bool sync_only,
+                       cudaStream_t st) {
+  cudaError_t e = hd::launch_prepare(pp, st);
+  if (e != cudaSuccess) return e;
+  if (self_sync) {
+    e = hd::launch_sync(dp, s, c->num_sms, st);
+    if (e == cudaSuccess && !sync_only) e = hd::launch_write(dp, s, c->num_sms, st);
+    return e;
+  }
+  return hd::launch_decode_two_phase(dp, s, c->num_sms, st);
+}
+
+uint32_t kernels_per_launch(bool self_sync, bool sync_only) {
+  return self_sync ? (sync_only ? 3u : 4u) : 3u;
+}
+
+// Queues a decode of fields that all use the same strategy with direct
+// kernel launches (sizes as kernel parameters).
+int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape& shape,
+                 bool self_sync, bool sync_only, cudaStream_t st) {
+  const uint32_t nf = static_cast<uint32_t>(descs.size());
+  Prepared P;
+  int rc = prepare_launch(c, descs, shape, self_sync, P);
+  if (rc) return rc;
+  const Layout L = make_layout(nf, P.tiles, P.subs, P.tab_bytes, P.s, self_sync,
+                               self_sync && !sync_only);
+  rc = ensure_ws(c, L.total);
+  if (rc) return rc;
+  char* ws = c->ws;
+  bind_descs(descs, ws, L, P, self_sync, sync_only);
+  if (nf > 1 && cudaMemcpyAsync(ws + L.desc, descs.data(), sizeof(FieldDesc) * nf,
+                                cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return HD_ERR_CUDA;
+  hd::PrepParams pp;
+  hd::DecodeParams dp;
+  make_params(descs, ws, L, P.s, self_sync, false, nf, P.tiles, pp, dp);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->profile) {
+    e0 = next_event(c);
+    e1 = next_event(c);
+  }
+  // the timed span starts after the table kernel
+  cudaError_t e = hd::launch_prepare(pp, st);
+  if (e == cudaSuccess && c->profile) cudaEventRecord(e0, st);
+  if (e == cudaSuccess) {
+    if (self_sync) {
+      e = hd::launch_sync(dp, P.s, c->num_sms, st);
+      if (e == cudaSuccess && !sync_only) e = hd::launch_write(dp, P.s, c->num_sms, st);
+    } else {
+      e = hd::launch_decode_two_phase(dp, P.s, c->num_sms, st);
+    }
+  }
+  if (c->profile) cudaEventRecord(e1, st);
+  if (e != cudaSuccess) return HD_ERR_CUDA;
+  c->launches += kernels_per_launch(self_sync, sync_only);
+  c->err_off = L.err;
+  c->err_count = nf;
+  c->last_shape = P.s;
+  return HD_OK;
+}
+
+// Queues the same work as one CUDA graph launch.  The graph is captured once
+// per (strategy, launch shape, capacity class) and replayed for every later
+// batch that fits: field and tile counts travel in the device-side launch
+// header and the descriptors, both copied in before the replay from pinned
+// host memory.  Capacities are powers of two, so a context holds few graphs.
+int queue_decode_graph(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape& shape,
+                       bool self_sync, cudaStream_t st) {
+  const uint32_t nf = static_cast<uint32_t>(descs.size());
+  Prepared P;
+  int rc = prepare_launch(c, descs, shape, self_sync, P);
+  if (rc) return rc;
+  const uint32_t cap_f = static_cast<uint32_t>(pow2_at_least(nf, 16));
+  const uint64_t cap_t = pow2_at_least(P.tiles, 1024);
+  const uint64_t cap_s = cap_t * P.s.threads;
+  const size_t cap_tab = static_cast<size_t>(pow2_at_least(P.tab_bytes, 1 << 16));
+  const Layout L = make_layout(cap_f, cap_t, cap_s, cap_tab, P.s, self_sync, self_sync);
+  rc = ensure_ws(c, L.total);
+  if (rc) return rc;
+  char* ws = c->ws;
+  bind_descs(descs, ws, L, P, self_sync, false);
+
+  // header + descriptors through pinned memory (wait until the previous copy
+  // out of it has run before overwriting it)
+  const size_t stage_bytes = 256 + sizeof(FieldDesc) * nf;
+  if (c->pinned_busy) {
+    if (cudaEventSynchronize(c->pinned_ev) != cudaSuccess) return HD_ERR_CUDA;
+    c->pinned_busy = false;
+  }
+  if (stage_bytes > c->pinned_cap) {
+    if (c->pinned) cudaFreeHost(c->pinned);
+    c->pinned = nullptr;
+    c->pinned_cap = 0;
+    const size_t cap = align_up(std::max<size_t>(stage_bytes, 64 << 10), 64 << 10);
+    if (cudaMallocHost(&c->pinned, cap) != cudaSuccess) {
+      cudaGetLastError();
+      return HD_ERR_NOMEM;
+    }
+    c->pinned_cap = cap;
+  }
+  hd::LaunchHeader h{};
+  h.total_units = P.tiles;
+  h.nfields = nf;
+  std::memset(c->pinned, 0, 256);
+  std::memcpy(c->pinned, &h, sizeof(h));
+  std::memcpy(c->pinned + 256, descs.data(), sizeof(FieldDesc) * nf);
+  if (cudaMemcpyAsync(ws + L.hdr, c->pinned, stage_bytes, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaEventRecord(c->pinned_ev, st) != cudaSuccess)
+    return HD_ERR_CUDA;
+  c->pinned_busy = true;
+
+  const GraphKey key{self_sync, P.s.S, P.s.threads, P.s.K, P.s.window, P.s.long_cap,
+                     cap_f, cap_t, cap_tab, reinterpret_cast<uintptr_t>(ws)};
+  auto it = c->graphs.find(key);
+  cudaGraphExec_t exec = nullptr;
+  if (it != c->graphs.end()) {
+    exec = it->second;
+  } else {
+    hd::PrepParams pp;
+    hd::DecodeParams dp;
+    make_params(descs, ws, L, P.s, self_sync, true, cap_f, cap_t, pp, dp);
+    if (!c->cap_stream &&
+        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return HD_ERR_CUDA;
+    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+      return HD_ERR_CUDA;
+    const cudaError_t le = launch_all(c, pp, dp, P.s, self_sync, false, c->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
+    if (le != cudaSuccess || ce != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return HD_ERR_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      cudaGetLastError();
+      return HD_ERR_CUDA;
+    }
+    c->graphs.emplace(key, exec);
+    c->captures += 1;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->profile) {
@@ -287,18 +494,13 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
     e1 = next_event(c);
     cudaEventRecord(e0, st);
   }
-  if (self_sync) {
-    e = hd::launch_sync(dp, s, c->num_sms, st);
-    if (e == cudaSuccess && !sync_only) e = hd::launch_write(dp, s, c->num_sms, st);
-  } else {
-    e = hd::launch_decode_two_phase(dp, s, c->num_sms, st);
-  }
+  const cudaError_t e = cudaGraphLaunch(exec, st);
   if (c->profile) cudaEventRecord(e1, st);
   if (e != cudaSuccess) return HD_ERR_CUDA;
-  c->launches += self_sync ? (sync_only ? 2 : 3) : 2;
-  c->err_off = err_off;
+  c->launches += kernels_per_launch(self_sync, false);
+  c->err_off = L.err;
   c->err_count = nf;
-  c->last_shape = s;
+  c->last_shape = P.s;
   return HD_OK;
 }
 
@@ -316,6 +518,122 @@ int read_errors(hd_ctx* c, void* stream, std::vector<uint32_t>& bits) {
       return HD_ERR_CUDA;
     }
   }
+  return HD_OK;
+}
+
+
+TuneKey tune_key(bool gap, uint32_t maxS, uint64_t bits, uint64_t syms) {
+  const double mean = static_cast<double>(bits) / static_cast<double>(syms ? syms : 1);
+  uint32_t lg = 0;
+  while ((1ull << (lg + 1)) <= syms) ++lg;
+  return TuneKey{!gap, static_cast<uint32_t>(mean * 4.0), lg, maxS};
+}
+
+// Launch shape of one strategy group of a batch: the context's configuration,
+// else the autotuned shape of the group's class, else the defaults.
+hd::LaunchShape group_shape(const hd_ctx* c, const hd_field* fs, const std::vector<uint32_t>& idx,
+                            bool gap) {
+  uint32_t maxS = 0;
+  uint64_t bits = 0, syms = 0;
+  for (uint32_t i : idx) {
+    maxS = std::max(maxS, fs[i].subseq_bits);
+    bits += fs[i].nbits;
+    syms += fs[i].n;
+  }
+  const hd_config& k = c->cfg;
+  const bool user = k.subseq_bits || k.threads || k.window || k.lut_bits;
+  hd_config use = k;
+  if (!user) {
+    auto it = c->tuned.find(tune_key(gap, maxS, bits, syms));
+    if (it != c->tuned.end()) use = it->second;
+  }
+  hd::LaunchShape s{};
+  s.S = use.subseq_bits ? use.subseq_bits : default_decoder_S(maxS ? maxS : 128, gap);
+  if (!gap && s.S > 256) s.S = 256;
+  s.threads = use.threads ? use.threads : kDefaultThreads;
+  s.K = use.lut_bits ? use.lut_bits : kDefaultK;
+  s.window = use.window;
+  return s;
+}
+
+struct BatchPlan {
+  std::vector<uint32_t> gap_i, sync_i;  // fields with work, by strategy
+};
+
+// Sorts the fields of a batch into the two strategy groups; fields with
+// nothing to decode (n == 0 and nbits == 0) are left out.
+int plan_batch(hd_ctx* c, const hd_field* fs, uint32_t nf, uint16_t* const* d_outs,
+               BatchPlan& plan) {
+  (void)c;
+  (void)d_outs;
+  for (uint32_t i = 0; i < nf; ++i) {
+    const hd_field* f = &fs[i];
+    if (f->n == 0 && f->nbits == 0) continue;
+    if (f->nbits == 0 || f->n == 0) return HD_ERR_CORRUPT;
+    (f->gap ? plan.gap_i : plan.sync_i).push_back(i);
+  }
+  return HD_OK;
+}
+
+// hd_decode_batch with the context lock held.  Each strategy group is one
+// graph launch; with both groups present the first group's error words are
+// read before the second reuses the workspace.
+int decode_batch_locked(hd_ctx* c, const hd_field* fs, uint32_t nf, uint16_t* const* d_outs,
+                        void* stream) {
+  c->err_count = 0;
+  c->host_status = HD_OK;
+  c->err_map.assign(nf, 0xffffffffu);
+  if (nf == 0) return HD_OK;
+  for (uint32_t i = 0; i < nf; ++i) {
+    const int rc = check_field(&fs[i], true, d_outs[i]);
+    if (rc == HD_PENDING) continue;
+    if (rc) {
+      c->host_status = rc;
+      return rc;
+    }
+  }
+  BatchPlan plan;
+  int rc = plan_batch(c, fs, nf, d_outs, plan);
+  if (rc == HD_ERR_CORRUPT) {
+    c->host_status = HD_ERR_CORRUPT;  // symbols without bits or bits without symbols
+    return HD_OK;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool both = !plan.gap_i.empty() && !plan.sync_i.empty();
+  std::vector<uint32_t> merged(nf, 0);
+  for (int grp = 0; grp < 2; ++grp) {
+    const bool ss = grp == 1;
+    const std::vector<uint32_t>& idx = ss ? plan.sync_i : plan.gap_i;
+    if (idx.empty()) continue;
+    const hd::LaunchShape s = group_shape(c, fs, idx, !ss);
+    std::vector<FieldDesc> d;
+    d.reserve(idx.size());
+    for (uint32_t i : idx) {
+      if (!ss && s.S % fs[i].subseq_bits) {
+        c->host_status = HD_ERR_ARG;
+        return HD_ERR_ARG;
+      }
+      FieldDesc x;
+      fill_desc(x, &fs[i], s, d_outs[i]);
+      d.push_back(x);
+    }
+    rc = queue_decode_graph(c, d, s, ss, st);
+    if (rc) {
+      c->host_status = rc;
+      return rc;
+    }
+    if (!both) {
+      for (size_t k = 0; k < idx.size(); ++k) c->err_map[idx[k]] = static_cast<uint32_t>(k);
+      return HD_OK;
+    }
+    std::vector<uint32_t> bits;
+    rc = read_errors(c, stream, bits);
+    if (rc) return rc;
+    for (size_t k = 0; k < idx.size(); ++k) merged[idx[k]] = bits[k];
+  }
+  // both groups ran: the per-field results are kept on the host
+  c->err_count = 0;
+  for (uint32_t i = 0; i < nf; ++i) c->err_map[i] = 0x80000000u | merged[i];
   return HD_OK;
 }
 
@@ -340,7 +658,11 @@ int hd_ctx_create(int device, hd_ctx** out) {
   if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) !=
           cudaSuccess ||
       cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) !=
-          cudaSuccess) {
+          cudaSuccess ||
+      cudaEventCreateWithFlags(&c->pinned_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&c->tune_ev[0]) != cudaSuccess ||
+      cudaEventCreate(&c->tune_ev[1]) != cudaSuccess) {
+    cudaGetLastError();
     delete c;
     return HD_ERR_CUDA;
   }
@@ -353,6 +675,12 @@ int hd_ctx_destroy(hd_ctx* c) {
   {
     DeviceGuard g(c->device);
     cudaDeviceSynchronize();
+    drop_graphs(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->pinned_ev) cudaEventDestroy(c->pinned_ev);
+    for (auto e : c->tune_ev)
+      if (e) cudaEventDestroy(e);
     if (c->ws) cudaFree(c->ws);
     if (c->stage) cudaFree(c->stage);
     for (auto e : c->events) cudaEventDestroy(e);
@@ -456,76 +784,97 @@ int hd_decode_batch(hd_ctx* c, const hd_field* fs, uint32_t nf, uint16_t* const*
   if (!c || (nf && (!fs || !d_outs))) return HD_ERR_ARG;
   std::lock_guard<std::mutex> lk(c->mu);
   DeviceGuard g(c->device);
-  c->err_count = 0;
-  c->host_status = HD_OK;
-  c->err_map.assign(nf, 0xffffffffu);
-  if (nf == 0) return HD_OK;
-  uint32_t maxS = 0;
+  return decode_batch_locked(c, fs, nf, d_outs, stream);
+}
+
+int hd_autotune(hd_ctx* c, const hd_field* fs, uint32_t nf, uint16_t* const* d_outs,
+                void* stream, hd_config* best) {
+  if (!c || !nf || !fs || !d_outs) return HD_ERR_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
   for (uint32_t i = 0; i < nf; ++i) {
-    int rc = check_field(&fs[i], true, d_outs[i]);
-    if (rc == HD_PENDING) continue;
-    if (rc) {
-      c->host_status = rc;
-      return rc;
-    }
-    maxS = std::max(maxS, fs[i].subseq_bits);
+    const int rc = check_field(&fs[i], true, d_outs[i]);
+    if (rc != HD_OK && rc != HD_PENDING) return rc;
   }
-  bool all_gap = true;
-  for (uint32_t i = 0; i < nf; ++i) all_gap &= fs[i].gap != nullptr;
-  hd::LaunchShape s = shape_for(c, maxS ? maxS : 128, all_gap);
-  std::vector<FieldDesc> gap_d, sync_d;
-  std::vector<uint32_t> gap_i, sync_i;
-  for (uint32_t i = 0; i < nf; ++i) {
-    const hd_field* f = &fs[i];
-    if (f->n == 0 && f->nbits == 0) continue;
-    if (f->nbits == 0 || f->n == 0 || (f->gap && s.S % f->subseq_bits)) {
-      c->host_status = f->nbits == 0 || f->n == 0 ? HD_ERR_CORRUPT : HD_ERR_ARG;
-      return c->host_status == HD_ERR_ARG ? HD_ERR_ARG : HD_OK;
-    }
-    FieldDesc d;
-    fill_desc(d, f, s, d_outs[i]);
-    if (f->gap) {
-      gap_d.push_back(d);
-      gap_i.push_back(i);
-    } else {
-      sync_d.push_back(d);
-      sync_i.push_back(i);
-    }
-  }
-  // Two strategy groups run as two launches; the error words of the first
-  // are copied aside so hd_batch_status sees both.
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  std::vector<uint32_t> merged;
-  if (!gap_d.empty() && !sync_d.empty()) {
-    // run sequentially with separate control regions: simplest is two queues
-    int rc = queue_decode(c, gap_d, s, false, false, st);
-    if (rc) return rc;
-    std::vector<uint32_t> bits;
-    rc = read_errors(c, stream, bits);
-    if (rc) return rc;
-    rc = queue_decode(c, sync_d, s, true, false, st);
-    if (rc) return rc;
-    std::vector<uint32_t> bits2;
-    rc = read_errors(c, stream, bits2);
-    if (rc) return rc;
-    c->err_map.assign(nf, 0xffffffffu);
-    // stash merged bits in host_status-only form: keep per-field map
-    merged.assign(nf, 0);
-    for (size_t k = 0; k < gap_i.size(); ++k) merged[gap_i[k]] = bits[k];
-    for (size_t k = 0; k < sync_i.size(); ++k) merged[sync_i[k]] = bits2[k];
-    // encode merged results as host-side per-field statuses
-    c->err_count = 0;
-    c->err_map.assign(nf, 0);
-    for (uint32_t i = 0; i < nf; ++i) c->err_map[i] = 0x80000000u | merged[i];
-    return HD_OK;
-  }
-  const bool ss = gap_d.empty();
-  std::vector<FieldDesc>& d = ss ? sync_d : gap_d;
-  std::vector<uint32_t>& idx = ss ? sync_i : gap_i;
-  int rc = queue_decode(c, d, s, ss, false, st);
+  BatchPlan plan;
+  int rc = plan_batch(c, fs, nf, d_outs, plan);
   if (rc) return rc;
-  for (size_t k = 0; k < idx.size(); ++k) c->err_map[idx[k]] = static_cast<uint32_t>(k);
-  return HD_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const hd_config saved = c->cfg;
+  const bool saved_profile = c->profile;
+  c->profile = false;
+  cudaEvent_t t0 = c->tune_ev[0], t1 = c->tune_ev[1];
+  bool first_group = true;
+  for (int grp = 0; grp < 2 && rc == HD_OK; ++grp) {
+    const bool ss = grp == 1;
+    const std::vector<uint32_t>& idx = ss ? plan.sync_i : plan.gap_i;
+    if (idx.empty()) continue;
+    uint32_t maxS = 0;
+    uint64_t bits = 0, syms = 0;
+    for (uint32_t i : idx) {
+      maxS = std::max(maxS, fs[i].subseq_bits);
+      bits += fs[i].nbits;
+      syms += fs[i].n;
+    }
+    const uint32_t S_list[4] = {64, 128, 256, 512};
+    const uint32_t B_list[3] = {128, 256, 512};
+    const uint32_t K_list[3] = {11, 12, 13};
+    double best_ms = 1e30;
+    hd_config best_cfg{};
+    for (uint32_t S : S_list) {
+      if (ss ? (S > 256) : (S < 128 || S % maxS)) continue;
+      for (uint32_t B : B_list) {
+        for (uint32_t K : K_list) {
+          c->cfg = hd_config{S, B, 0, K};
+          std::vector<FieldDesc> d;
+          const hd::LaunchShape sh = group_shape(c, fs, idx, !ss);
+          for (uint32_t i : idx) {
+            FieldDesc x;
+            fill_desc(x, &fs[i], sh, d_outs[i]);
+            d.push_back(x);
+          }
+          double ms = 1e30;
+          bool ok = true;
+          for (int rep = 0; rep < 4 && ok; ++rep) {
+            std::vector<FieldDesc> dd = d;
+            cudaEventRecord(t0, st);
+            const int r = queue_decode_graph(c, dd, sh, ss, st);
+            cudaEventRecord(t1, st);
+            if (r) {
+              ok = false;
+              break;
+            }
+            std::vector<uint32_t> bits_v;
+            if (read_errors(c, stream, bits_v) != HD_OK) {
+              ok = false;
+              break;
+            }
+            for (uint32_t b : bits_v) ok &= b == 0;
+            float t = 0;
+            cudaEventElapsedTime(&t, t0, t1);
+            if (rep) ms = std::min(ms, static_cast<double>(t));
+          }
+          if (ok && ms < best_ms) {
+            best_ms = ms;
+            best_cfg = hd_config{S, B, 0, K};
+          }
+        }
+      }
+    }
+    if (best_ms >= 1e30) {
+      rc = HD_ERR_CORRUPT;  // no candidate decoded the batch cleanly
+      break;
+    }
+    c->tuned[tune_key(!ss, maxS, bits, syms)] = best_cfg;
+    if (first_group && best) *best = best_cfg;
+    first_group = false;
+  }
+  c->cfg = saved;
+  c->profile = saved_profile;
+  drop_graphs(c);  // keep only what later batches use (recaptured on demand)
+  c->err_count = 0;
+  c->err_map.clear();
+  return rc;
 }
 
 int hd_batch_status(hd_ctx* c, int32_t* status, uint32_t nf, void* stream) {
@@ -625,5 +974,13 @@ int hd_kernel_time(hd_ctx* c, double* ms, uint64_t* launches) {
 }
 
 uint64_t hd_launch_count(hd_ctx* c) { return c ? c->launches : 0; }
+
+int hd_graph_stats(hd_ctx* c, uint64_t* captures, uint32_t* cached) {
+  if (!c || !captures || !cached) return HD_ERR_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  *captures = c->captures;
+  *cached = static_cast<uint32_t>(c->graphs.size());
+  return HD_OK;
+}
 
 }  // extern "C"

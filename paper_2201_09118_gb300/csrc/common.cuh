@@ -66,9 +66,20 @@ enum : uint32_t {
   kErrTable = 32u,   // invalid code-length table
 };
 
+// Sizes of a launch kept in device memory.  Graph launches read their field
+// and tile counts from here (the host rewrites it before every replay), so one
+// captured graph serves every batch within the capacity it was captured for.
+struct LaunchHeader {
+  uint64_t total_units;  // tiles
+  uint32_t nfields;
+  uint32_t pad;
+};
+
 struct DecodeParams {
-  FieldDesc f0;             // the field when nfields == 1
-  const FieldDesc* fields;  // device array when nfields > 1
+  FieldDesc f0;             // the field when nfields == 1 and hdr == NULL
+  const FieldDesc* fields;  // device array (always used when hdr != NULL)
+  const LaunchHeader* hdr;  // non-NULL: nfields and total_units are read from here;
+                            // the two fields below then hold the capacity
   uint32_t nfields;
   uint32_t K;               // first-level table bits for this launch
   uint32_t window;          // shared-memory output window, symbols (Alg. 1 buffer)
@@ -90,7 +101,9 @@ struct DecodeParams {
 struct PrepParams {
   FieldDesc f0;
   const FieldDesc* fields;
-  uint32_t nfields;
+  const LaunchHeader* hdr;  // as in DecodeParams
+  uint32_t nfields;         // field count, or the capacity when hdr != NULL
+  uint32_t table_blocks;    // blocks that build tables (each loops over fields)
   uint32_t K;
   uint4* zero_ptr;          // region cleared before the decode kernel
   uint64_t zero_vec;        // its size in 16-byte vectors

@@ -138,18 +138,19 @@ __global__ void __launch_bounds__(B) k_decode(const __grid_constant__ DecodePara
   uint32_t cur_field = 0xffffffffu;
   uint32_t* col = s_bits + t;
   uint16_t* scr = s_scr + t;
+  const LaunchSize LS = launch_size(P);
 
   for (;;) {
     if (t == 0) {
       const uint32_t g = atomicAdd(P.ticket, 1u);
       s_ticket = g;
-      s_field = g < P.total_units ? find_field(P, g) : 0u;
+      s_field = g < LS.units ? find_field(P, LS, g) : 0u;
     }
     __syncthreads();
     const uint64_t g = s_ticket;
-    if (g >= P.total_units) break;
+    if (g >= LS.units) break;
     const uint32_t fi = s_field;
-    const FieldDesc& F = field_of(P, fi);
+    const FieldDesc& F = field_of(P, LS, fi);
     if (fi != cur_field) {
       load_table(F.table, P.K, s_lut, s_end, s_base, s_meta, B, s_long, P.long_cap);
       cur_field = fi;

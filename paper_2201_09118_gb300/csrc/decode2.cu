@@ -76,9 +76,10 @@ __global__ void __launch_bounds__(B) k_count(const __grid_constant__ DecodeParam
   const int t = threadIdx.x;
   uint32_t* col = s_bits + t;
   uint32_t cur_field = 0xffffffffu;
-  for (uint64_t g = blockIdx.x; g < P.total_units; g += gridDim.x) {
-    const uint32_t fi = find_field(P, g);
-    const FieldDesc& F = field_of(P, fi);
+  const LaunchSize LS = launch_size(P);
+  for (uint64_t g = blockIdx.x; g < LS.units; g += gridDim.x) {
+    const uint32_t fi = find_field(P, LS, g);
+    const FieldDesc& F = field_of(P, LS, fi);
     if (fi != cur_field) {
       __syncthreads();
       load_table(F.table, P.K, s_lut, s_end, s_base, s_meta, B, s_long, P.long_cap);
@@ -170,9 +171,10 @@ __global__ void __launch_bounds__(B) k_write(const __grid_constant__ DecodeParam
   const int warp = t >> 5;
   uint32_t* col = s_bits + t;
   uint32_t cur_field = 0xffffffffu;
-  for (uint64_t g = blockIdx.x; g < P.total_units; g += gridDim.x) {
-    const uint32_t fi = find_field(P, g);
-    const FieldDesc& F = field_of(P, fi);
+  const LaunchSize LS = launch_size(P);
+  for (uint64_t g = blockIdx.x; g < LS.units; g += gridDim.x) {
+    const uint32_t fi = find_field(P, LS, g);
+    const FieldDesc& F = field_of(P, LS, fi);
     if (fi != cur_field) {
       __syncthreads();
       load_table(F.table, P.K, s_lut, s_end, s_base, s_meta, B, s_long, P.long_cap);

@@ -228,14 +228,29 @@ __device__ __forceinline__ void load_table(const TableHeader* H, uint32_t K, uin
   }
 }
 
-__device__ __forceinline__ const FieldDesc& field_of(const DecodeParams& P, uint32_t f) {
-  return P.nfields == 1 ? P.f0 : P.fields[f];
+// Field and tile counts of this launch (kernel parameters, or the device-side
+// header of a graph launch).
+struct LaunchSize {
+  uint64_t units;
+  uint32_t nfields;
+  bool single;  // the one field is the kernel parameter f0
+};
+
+__device__ __forceinline__ LaunchSize launch_size(const DecodeParams& P) {
+  if (P.hdr) return {P.hdr->total_units, P.hdr->nfields, false};
+  return {P.total_units, P.nfields, P.nfields == 1};
+}
+
+__device__ __forceinline__ const FieldDesc& field_of(const DecodeParams& P, const LaunchSize& L,
+                                                     uint32_t f) {
+  return L.single ? P.f0 : P.fields[f];
 }
 
 // Index of the field whose work units contain unit g (fields are in order).
-__device__ __forceinline__ uint32_t find_field(const DecodeParams& P, uint64_t g) {
-  if (P.nfields == 1) return 0;
-  uint32_t lo = 0, hi = P.nfields - 1;
+__device__ __forceinline__ uint32_t find_field(const DecodeParams& P, const LaunchSize& L,
+                                               uint64_t g) {
+  if (L.nfields <= 1) return 0;
+  uint32_t lo = 0, hi = L.nfields - 1;
   while (lo < hi) {
     const uint32_t mid = (lo + hi + 1) >> 1;
     if (P.fields[mid].unit_begin <= g) lo = mid;

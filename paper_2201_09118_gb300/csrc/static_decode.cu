@@ -125,6 +125,7 @@ extern "C" int hd_decode_static(const hd_field* f, uint16_t* d_out, void* stream
   pp.f0 = d;
   pp.fields = nullptr;
   pp.nfields = 1;
+  pp.table_blocks = 1;
   pp.K = s.K;
   pp.zero_ptr = reinterpret_cast<uint4*>(scratch);
   pp.zero_vec = zero_bytes / 16;

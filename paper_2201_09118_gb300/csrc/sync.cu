@@ -232,9 +232,10 @@ __global__ void __launch_bounds__(B) k_sync(const __grid_constant__ DecodeParams
   const SyncShared sh{s_warp, s_e_last, s_x};
 
   uint32_t cur_field = 0xffffffffu;
-  for (uint64_t g = blockIdx.x; g < P.total_units; g += gridDim.x) {
-    const uint32_t fi = find_field(P, g);
-    const FieldDesc& F = field_of(P, fi);
+  const LaunchSize LS = launch_size(P);
+  for (uint64_t g = blockIdx.x; g < LS.units; g += gridDim.x) {
+    const uint32_t fi = find_field(P, LS, g);
+    const FieldDesc& F = field_of(P, LS, fi);
     if (fi != cur_field) {
       __syncthreads();
       load_table(F.table, P.K, s_lut, s_end, s_base, s_meta, B, s_long, P.long_cap);
@@ -290,7 +291,7 @@ __device__ __forceinline__ uint64_t first_broken(const DecodeParams& P, uint64_t
   return f;
 }
 
-// One block per field: finds, in order, every tile whose assumed start is not
+// One block per field (blocks loop over fields): finds, in order, every tile whose assumed start is not
 // where its predecessor stopped and synchronises it again from the true start
 // (which can move its own stop, so the scan resumes right after it); then
 // checks that the field's last subsequence ended at nbits.
@@ -312,34 +313,36 @@ __global__ void __launch_bounds__(B) k_fix(const __grid_constant__ DecodeParams 
   __shared__ unsigned long long s_first;
   const SyncShared sh{s_warp, s_e_last, s_x};
 
-  const uint32_t fi = blockIdx.x;
-  if (fi >= P.nfields) return;
-  const FieldDesc& F = field_of(P, fi);
-  if (F.nunits == 0) return;
-  load_table(F.table, P.K, s_lut, s_end, s_base, s_meta, B, s_long, P.long_cap);
-  __syncthreads();
-  const Tables T{s_lut,
-                 s_end,
-                 s_base,
-                 reinterpret_cast<const uint16_t*>(reinterpret_cast<const char*>(F.table) +
-                                                   kTableHeaderBytes + (4u << P.K)),
-                 s_long,
-                 s_meta[2],
-                 P.long_cap,
-                 s_meta[0],
-                 32u - P.K};
-  const bool table_ok = s_meta[1] == 0;
-  const uint64_t g0 = F.unit_begin, g1 = F.unit_begin + F.nunits;
-  uint64_t cursor = g0 + 1;
-  while (table_ok && cursor < g1) {
-    const uint64_t gb = first_broken<B>(P, cursor, g1, &s_first);
-    if (gb >= g1) break;
-    sync_tile<S, B>(P, F, T, table_ok, gb, false, P.tile_e[gb], s_bits, s_pre, sh, true);
-    cursor = gb + 1;
-  }
-  if (threadIdx.x == 0) {
-    if (!table_ok) atomicOr(F.err, kErrTable);
-    else if (P.tile_flag[g1 - 1]) atomicOr(F.err, kErrCode);
+  const LaunchSize LS = launch_size(P);
+  for (uint32_t fi = blockIdx.x; fi < LS.nfields; fi += gridDim.x) {
+    const FieldDesc& F = field_of(P, LS, fi);
+    if (F.nunits == 0) continue;
+    __syncthreads();  // the previous field's table is no longer read
+    load_table(F.table, P.K, s_lut, s_end, s_base, s_meta, B, s_long, P.long_cap);
+    __syncthreads();
+    const Tables T{s_lut,
+                   s_end,
+                   s_base,
+                   reinterpret_cast<const uint16_t*>(reinterpret_cast<const char*>(F.table) +
+                                                     kTableHeaderBytes + (4u << P.K)),
+                   s_long,
+                   s_meta[2],
+                   P.long_cap,
+                   s_meta[0],
+                   32u - P.K};
+    const bool table_ok = s_meta[1] == 0;
+    const uint64_t g0 = F.unit_begin, g1 = F.unit_begin + F.nunits;
+    uint64_t cursor = g0 + 1;
+    while (table_ok && cursor < g1) {
+      const uint64_t gb = first_broken<B>(P, cursor, g1, &s_first);
+      if (gb >= g1) break;
+      sync_tile<S, B>(P, F, T, table_ok, gb, false, P.tile_e[gb], s_bits, s_pre, sh, true);
+      cursor = gb + 1;
+    }
+    if (threadIdx.x == 0) {
+      if (!table_ok) atomicOr(F.err, kErrTable);
+      else if (P.tile_flag[g1 - 1]) atomicOr(F.err, kErrCode);
+    }
   }
 }
 
@@ -365,7 +368,9 @@ cudaError_t launch_sb(const DecodeParams& p, const LaunchShape& s, int num_sms,
   ks<<<static_cast<unsigned>(grid), B, smem, stream>>>(p);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  kf<<<p.nfields, B, smem, stream>>>(p);
+  const uint32_t fix_grid = p.nfields < 1024u ? p.nfields : 1024u;
+  if (fix_grid == 0) return cudaSuccess;
+  kf<<<fix_grid, B, smem, stream>>>(p);
   return cudaGetLastError();
 }
 

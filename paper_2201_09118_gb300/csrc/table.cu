@@ -17,8 +17,8 @@ namespace {
 
 constexpr int kPrepThreads = 1024;
 
-__device__ __forceinline__ const FieldDesc& field_at(const PrepParams& p, uint32_t i) {
-  return p.nfields == 1 ? p.f0 : p.fields[i];
+__device__ __forceinline__ const FieldDesc& field_at(const PrepParams& p, bool single, uint32_t i) {
+  return single ? p.f0 : p.fields[i];
 }
 
 // One block builds the table of one field.
@@ -139,12 +139,17 @@ __device__ void build_table(const FieldDesc& F, uint32_t K) {
 
 __global__ void __launch_bounds__(kPrepThreads) k_prepare(const __grid_constant__ PrepParams P) {
   const uint32_t b = blockIdx.x;
-  if (b < P.nfields) {
-    build_table(field_at(P, b), P.K);
+  if (b < P.table_blocks) {
+    const uint32_t nf = P.hdr ? P.hdr->nfields : P.nfields;
+    const bool single = !P.hdr && P.nfields == 1;
+    for (uint32_t f = b; f < nf; f += P.table_blocks) {
+      __syncthreads();  // the previous field's shared state is no longer read
+      build_table(field_at(P, single, f), P.K);
+    }
     return;
   }
-  // clear the per-launch control region (tickets, error words, look-back states)
-  const uint64_t zb = b - P.nfields;
+  // clear the per-launch control region (error words, segment totals)
+  const uint64_t zb = b - P.table_blocks;
   const uint4 z = make_uint4(0, 0, 0, 0);
   for (uint64_t i = zb * kPrepThreads + threadIdx.x; i < P.zero_vec;
        i += static_cast<uint64_t>(P.zero_blocks) * kPrepThreads)
@@ -155,7 +160,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prepare(const __grid_constant_
 
 cudaError_t launch_prepare(const PrepParams& p, cudaStream_t stream) {
   const uint32_t zb = p.zero_blocks;
-  const uint32_t grid = p.nfields + zb;
+  const uint32_t grid = p.table_blocks + zb;
   if (grid == 0) return cudaSuccess;
   k_prepare<<<grid, kPrepThreads, 0, stream>>>(p);
   return cudaGetLastError();

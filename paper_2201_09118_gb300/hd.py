@@ -80,6 +80,10 @@ _SIGS = {
     "hd_kernel_time": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
                        ctypes.c_int),
     "hd_launch_count": ([_P], ctypes.c_uint64),
+    "hd_autotune": ([_P, ctypes.POINTER(hd_field), ctypes.c_uint32, _P, _P,
+                     ctypes.POINTER(hd_config)], ctypes.c_int),
+    "hd_graph_stats": ([_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32)],
+                       ctypes.c_int),
     "hd_version": ([], ctypes.c_char_p),
 }
 
@@ -253,6 +257,25 @@ class Context:
         ptrs = (ctypes.c_void_p * max(1, nf))(*[o.data_ptr() for o in outs])
         _check("hd_decode_batch", self._lib.hd_decode_batch(self.handle, arr, nf, ptrs,
                                                              _stream_handle(stream)))
+
+    def autotune(self, fields: Sequence[DeviceField], outs, stream=None) -> dict:
+        """Times every candidate launch shape on this batch and keeps the fastest
+        for the batch's class; returns it."""
+        nf = len(fields)
+        arr = (hd_field * max(1, nf))(*[f.c_struct() for f in fields])
+        ptrs = (ctypes.c_void_p * max(1, nf))(*[o.data_ptr() for o in outs])
+        cfg = hd_config()
+        _check("hd_autotune", self._lib.hd_autotune(self.handle, arr, nf, ptrs,
+                                                    _stream_handle(stream), ctypes.byref(cfg)))
+        return {"subseq_bits": cfg.subseq_bits, "threads": cfg.threads, "window": cfg.window,
+                "lut_bits": cfg.lut_bits}
+
+    def graph_stats(self):
+        cap = ctypes.c_uint64()
+        cached = ctypes.c_uint32()
+        _check("hd_graph_stats", self._lib.hd_graph_stats(self.handle, ctypes.byref(cap),
+                                                          ctypes.byref(cached)))
+        return cap.value, cached.value
 
     def batch_status(self, nf: int, stream=None):
         st = np.zeros(max(1, nf), dtype=np.int32)
