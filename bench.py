@@ -1,11 +1,17 @@
 #!/usr/bin/env python
-"""Benchmark: decoded GB/s of canonical-Huffman decoding of a 512^3 field of
-Lorenzo quantization codes on GB300, through the library's C ABI.
+"""Benchmark: decoded GB/s of canonical-Huffman decoding on GB300 through the
+library's C ABI.
 
-One step = one hd_decode of the whole field (decode-table kernel + persistent
-gap-array decode kernel), inputs resident in HBM, L2 flushed between steps.
-Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
-instead (bounded samples of the same workload on the host cores).
+Headline (`value`): one step = one hd_decode of a 512^3 field of Lorenzo
+quantization codes with its gap array (decode-table kernel, count kernel,
+decode-and-write kernel), inputs resident in HBM, L2 flushed between steps.
+Extra keys: the same field by self-synchronisation, end to end from pinned
+host buffers (`e2e`), the batched workload (256 fields of uneven sizes, one
+graph launch, autotuned shape) against one launch per field (`batched`), and
+a served request trace (Poisson arrivals, continuous batching, p50/p99
+latency) against one launch per request (`served`).  Prints one JSON line
+(rank 0).  ``--impl reference`` times the CPU oracle instead (bounded samples
+of the same workload on the host cores).
 
 Multi-GPU (torchrun): every rank decodes its own field of the same shape
 (replicas, no collective on the data path); value = all ranks' symbols / the
@@ -195,7 +201,152 @@ def run_reference(args):
     return 0
 
 
+def make_batch_field(spec):
+    """Pool worker: one field of the batched workload, encoded on the host
+    (product encoder, own codebook).  Returns the stream and a CRC of the codes."""
+    import zlib
+
+    import synth
+    from paper_2201_09118_gb300 import hd
+    x = synth.smooth_codes_1d(spec.n, spec.rel_eb, alphabet=spec.alphabet, seed=spec.seed)
+    lengths = hd.hd_build_codebook(x, spec.alphabet, 32)
+    enc = hd.hd_encode(x, lengths, 128)
+    return {"words": enc["words"], "gap": enc["gap"], "nbits": enc["nbits"],
+            "nwords": enc["nwords"], "subseq_bits": 128, "lengths": lengths, "n": int(x.size),
+            "alphabet": spec.alphabet, "rel_eb": spec.rel_eb, "crc": zlib.crc32(x.tobytes())}
+
+
+def start_batch_generation(n_fields: int, procs: int):
+    """Starts encoding the batched workload in a spawn pool (before any CUDA
+    call in this process); returns (pool, async result)."""
+    import multiprocessing as mp
+
+    import synth
+    specs = synth.batch_spec(n_fields, lo=1 << 16, hi=1 << 26, seed=1003)
+    pool = mp.get_context("spawn").Pool(procs)
+    # largest fields first so the pool finishes evenly
+    order = sorted(range(len(specs)), key=lambda k: -specs[k].n)
+    res = pool.map_async(make_batch_field, [specs[k] for k in order], chunksize=1)
+    return pool, res, order
+
+
+def run_batched(hd, torch, dev, stream, flush, fields_h, steps: int):
+    """Config-3 leg: all fields in one graph launch (autotuned shape) against
+    one hd_decode launch per field, same outputs."""
+    import zlib
+    fields = [hd.DeviceField.upload(f, f["lengths"], f["n"], device=f"cuda:{dev}")
+              for f in fields_h]
+    outs = [torch.empty(max(1, f["n"]), dtype=torch.int16, device=f"cuda:{dev}")
+            for f in fields_h]
+    total = sum(f["n"] for f in fields_h)
+    ctx = hd.Context(dev)
+    t0 = time.perf_counter()
+    best = ctx.autotune(fields, outs, stream)
+    tune_s = time.perf_counter() - t0
+    bad = [k for k, (f, o) in enumerate(zip(fields_h, outs))
+           if zlib.crc32(o[:f["n"]].cpu().numpy().tobytes()) != f["crc"]]
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    l0 = ctx.launch_count()
+    ms_b = timed(lambda: ctx.decode_batch(fields, outs, stream))
+    rc_b, _ = ctx.batch_status(len(fields), stream)
+    launches_b = (ctx.launch_count() - l0) // (steps + 1)
+
+    def per_field():
+        for f, o in zip(fields, outs):
+            ctx.decode(f, o, stream)
+    ms_p = timed(per_field)
+    st_p = ctx.status(stream)
+    caps, cached = ctx.graph_stats()
+    ctx.close()
+    return {"value": 2.0 * total / (ms_b * 1e-3) / 1e9, "unit": "GB/s", "fields": len(fields_h),
+            "codes": total, "ms_per_batch": ms_b, "kernels_per_batch": launches_b,
+            "per_field": {"value": 2.0 * total / (ms_p * 1e-3) / 1e9, "unit": "GB/s",
+                          "ms": ms_p, "status_last": st_p},
+            "speedup_vs_per_field": ms_p / ms_b, "autotuned": best, "tune_s": tune_s,
+            "graphs_captured": caps, "status": rc_b, "crc_mismatches": len(bad),
+            "workload": "256 1D fields, codes log-uniform in [2^16, 2^26], alphabets "
+                        "{256,1024,4096}, rel. error bound log-uniform in [1e-6, 1e-2], own "
+                        "codebook each, S=128 gap arrays; L2 flushed between steps"}, fields
+
+
+def serve_trace(hd, dev, fields, arrivals, ids, sizes, direct: bool, shape):
+    """Replays one request trace through a server; returns throughput and
+    latency percentiles (latency = submission to observed completion)."""
+    srv = hd.Server(dev, budget_bytes=40 << 30, slots=1 if direct else 2,
+                    max_batch=1 if direct else 64, direct=direct, shape=shape)
+    fid = [srv.register(f) for f in fields]
+    n_req = len(ids)
+    lat = np.zeros(n_req)
+    status_bad = 0
+    tick_req = {}
+    i = done = 0
+    t0 = time.perf_counter()
+    while done < n_req:
+        now = time.perf_counter() - t0
+        while i < n_req and arrivals[i] <= now:
+            tick_req[srv.submit(fid[ids[i]])] = i
+            i += 1
+        for t in srv.completed():
+            t = int(t)
+            r = srv.poll(t)
+            lat[tick_req.pop(t)] = r["latency_us"]
+            status_bad += r["status"] != 0
+            srv.release(t)
+            done += 1
+    span = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    out_bytes = 2.0 * float(np.sum(sizes[ids]))
+    return {"throughput_gbps": out_bytes / span / 1e9, "requests_per_s": n_req / span,
+            "p50_ms": float(np.percentile(lat, 50)) / 1e3,
+            "p99_ms": float(np.percentile(lat, 99)) / 1e3, "span_s": span,
+            "batches": st["batches"], "peak_budget_bytes": st["peak_bytes"],
+            "bad_status": int(status_bad)}
+
+
+def run_served(hd, dev, fields, batch_ms: float, n_req: int, shape):
+    """Config-4 leg: Poisson arrivals at 0.8x the batched capacity over the
+    resident pool, batched server vs one launch per request; plus both at
+    saturation (all requests queued at once)."""
+    sizes = np.array([f.n for f in fields], dtype=np.float64)
+    rng = np.random.default_rng(1004)
+    ids = rng.integers(0, len(fields), size=n_req)
+    capacity = len(fields) / (batch_ms * 1e-3)  # requests/s when decoding in full batches
+    rate = 0.8 * capacity
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    zero = np.zeros(n_req)
+    out = {"requests": n_req, "arrival": "Poisson", "rate_rps": rate, "load": 0.8,
+           "capacity_rps": capacity, "budget_bytes": 40 << 30,
+           "pool": f"{len(fields)} resident fields of the batched workload"}
+    out["batched"] = serve_trace(hd, dev, fields, arrivals, ids, sizes, False, shape)
+    out["per_request"] = serve_trace(hd, dev, fields, arrivals, ids, sizes, True, None)
+    out["saturated"] = {
+        "batched": serve_trace(hd, dev, fields, zero, ids, sizes, False, shape),
+        "per_request": serve_trace(hd, dev, fields, zero, ids, sizes, True, None)}
+    out["value"] = out["batched"]["throughput_gbps"]
+    out["unit"] = "GB/s"
+    return out
+
+
 def run_gpu(args):
+    gen = None
+    if not args.no_batch and _env_int("RANK", 0) == 0:
+        gen = start_batch_generation(args.batch_fields, max(1, min(16, os.cpu_count() or 1)))
     import torch
     from paper_2201_09118_gb300 import hd
 
@@ -217,6 +368,18 @@ def run_gpu(args):
     n = codes.size
     lengths = hd.hd_build_codebook(codes, 1024, 32)
     enc = hd.hd_encode(codes, lengths, 128)
+    fields_h = None
+    if gen is not None:
+        # the batched workload is encoded by the pool meanwhile; collect it
+        # before anything is timed so that no host work overlaps a timing
+        pool, res, order = gen
+        got = res.get()
+        pool.close()
+        pool.join()
+        fields_h = [None] * len(got)
+        for k, f in zip(order, got):
+            fields_h[k] = f
+        del got
     field = hd.DeviceField.upload(enc, lengths, n, device=f"cuda:{dev}")
     field_ss = hd.DeviceField(field.words, field.nbits, None, 128, field.lengths, 1024, n)
     out = torch.empty(n, dtype=torch.int16, device=f"cuda:{dev}")
@@ -309,6 +472,13 @@ def run_gpu(args):
             dist.destroy_process_group()
         return 0
 
+    extra = {}
+    if fields_h is not None:
+        batched, dev_fields = run_batched(hd, torch, dev, stream, flush, fields_h, 3)
+        extra["batched"] = batched
+        extra["served"] = run_served(hd, dev, dev_fields, batched["ms_per_batch"],
+                                     args.requests, batched["autotuned"])
+
     nbytes_alg = (enc["nbits"] + 7) // 8 + enc["nsub"] + 2 * n
     kernel_ms = kms / max(1, kl)
     achieved = nbytes_alg / (kernel_ms * 1e-3) / 1e9
@@ -334,6 +504,7 @@ def run_gpu(args):
         "selfsync": {"value": 2.0 * n * max(3, args.steps // 2) * world / (ms_ss * 1e-3) / 1e9,
                      "unit": "GB/s", "kernel_ms": kms_ss / max(1, kl_ss), "status": st_ss},
     }
+    line.update(extra)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(codes)
     print(json.dumps(line), flush=True)
@@ -385,6 +556,10 @@ def main():
     ap.add_argument("--lut-bits", dest="lut_bits", type=int, default=0)
     ap.add_argument("--subseq-bits", dest="subseq_bits", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched (256 fields) and served (request trace) legs")
+    ap.add_argument("--batch-fields", dest="batch_fields", type=int, default=256)
+    ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--profile-strategy", choices=["gap", "selfsync"], default=None,
                     help="decode one strategy only and print its kernel time (profiler runs)")
     args = ap.parse_args()

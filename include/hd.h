@@ -216,6 +216,75 @@ int hd_decode_host(hd_ctx* ctx, const hd_field* f, uint16_t* host_out, void* str
  * The paper has no counterpart to this entry point. */
 int hd_decode_static(const hd_field* f, uint16_t* d_out, void* stream);
 
+/* ---- serving loop ------------------------------------------------------- */
+
+/* A server decodes requests against resident fields: each request names a
+ * registered field and receives a fresh device copy of its symbols.  One
+ * worker thread keeps up to `slots` batches in flight, each on its own stream
+ * with its own decode context, so requests that arrive while others are on
+ * the GPU are admitted as soon as a slot and budget memory are free and their
+ * work overlaps the running batches (continuous batching).  Admission is
+ * first come, first served: the oldest pending requests whose outputs fit the
+ * budget (up to max_batch) form the next batch, which is decoded by one
+ * hd_decode_batch call.  The paper has no counterpart to the server; each
+ * batch runs the paper's decoders (Sec. III-B/III-C, Algorithm 1). */
+typedef struct hd_server hd_server;
+
+typedef struct hd_serve_config {
+  uint64_t budget_bytes; /* device memory for request outputs (one allocation at
+                            creation; a request is admitted only when its
+                            2*n-byte output fits what is not yet released) */
+  uint32_t slots;        /* batches in flight at once, 1 .. 8 */
+  uint32_t max_batch;    /* requests per batch, 1 .. 4096 */
+  uint32_t queue_cap;    /* pending requests before submit returns HD_ERR_BUSY
+                            (0 = 2^20) */
+  uint32_t direct;       /* 1: one hd_decode launch per request instead of a
+                            batch (requires max_batch == 1; the baseline the
+                            batched server is compared with) */
+} hd_serve_config;
+
+typedef struct hd_result {
+  int32_t status;        /* decode status of the request */
+  const uint16_t* d_out; /* device pointer to its n symbols, valid until release */
+  uint64_t n;
+  double queue_us;       /* submission to launch */
+  double latency_us;     /* submission to observed completion */
+} hd_result;
+
+typedef struct hd_serve_stats_t {
+  uint64_t submitted, completed, batches, pending, in_flight;
+  uint64_t budget_bytes, used_bytes, peak_bytes;
+} hd_serve_stats_t;
+
+/* Creates a server on `device` (`shape` may be NULL: default or autotuned
+ * launch shapes; else the shape every slot uses).  HD_ERR_ARG for a config
+ * outside the ranges above, HD_ERR_NOMEM if the budget cannot be allocated. */
+int hd_serve_create(int device, const hd_serve_config* cfg, const hd_config* shape,
+                    hd_server** out);
+/* Drops pending requests (their status becomes HD_ERR_BUSY), waits for the
+ * batches in flight, frees everything (outputs included). */
+int hd_serve_destroy(hd_server* srv);
+/* Registers a resident field (device pointers, as for hd_decode; they stay
+ * owned by the caller and must outlive the server).  Returns its id. */
+int hd_serve_register(hd_server* srv, const hd_field* f, uint32_t* field_id);
+/* Queues a decode of field `field_id`; returns at once with a ticket.
+ * HD_ERR_BUSY if the queue is full, HD_ERR_NOMEM if the output can never fit
+ * the budget. */
+int hd_serve_submit(hd_server* srv, uint32_t field_id, uint64_t* ticket);
+/* HD_PENDING while the request is queued or on the GPU; HD_OK with *res
+ * filled once it completed (res->status holds its decode status). */
+int hd_serve_poll(hd_server* srv, uint64_t ticket, hd_result* res);
+/* Returns a completed request's output memory to the budget and forgets the
+ * ticket (HD_ERR_BUSY if it has not completed). */
+int hd_serve_release(hd_server* srv, uint64_t ticket);
+/* Hands out up to `cap` tickets of requests that completed since the last
+ * call (in completion order); *count receives how many. */
+int hd_serve_completed(hd_server* srv, uint64_t* tickets, uint32_t cap, uint32_t* count);
+/* Waits until no request is pending or in flight.  Requests wait for budget
+ * memory, so outputs must be released meanwhile if the budget is short. */
+int hd_serve_drain(hd_server* srv);
+int hd_serve_stats(hd_server* srv, hd_serve_stats_t* out);
+
 /* Kernel timing: when enabled, the context records CUDA events around every
  * main decode kernel it launches.  hd_kernel_time waits for them and returns
  * the summed device time in milliseconds and the launch count, then clears. */

@@ -57,6 +57,23 @@ class hd_config(ctypes.Structure):
                 ("window", ctypes.c_uint32), ("lut_bits", ctypes.c_uint32)]
 
 
+class hd_serve_config(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32),
+                ("max_batch", ctypes.c_uint32), ("queue_cap", ctypes.c_uint32),
+                ("direct", ctypes.c_uint32)]
+
+
+class hd_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("d_out", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("queue_us", ctypes.c_double), ("latency_us", ctypes.c_double)]
+
+
+class hd_serve_stats_t(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "completed", "batches", "pending",
+                                                "in_flight", "budget_bytes", "used_bytes",
+                                                "peak_bytes")]
+
+
 # every exported symbol of include/hd.h with its ctypes signature
 _P = ctypes.c_void_p
 _SIGS = {
@@ -84,6 +101,18 @@ _SIGS = {
                      ctypes.POINTER(hd_config)], ctypes.c_int),
     "hd_graph_stats": ([_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32)],
                        ctypes.c_int),
+    "hd_serve_create": ([ctypes.c_int, ctypes.POINTER(hd_serve_config), ctypes.POINTER(hd_config),
+                         ctypes.POINTER(_P)], ctypes.c_int),
+    "hd_serve_destroy": ([_P], ctypes.c_int),
+    "hd_serve_register": ([_P, ctypes.POINTER(hd_field), ctypes.POINTER(ctypes.c_uint32)],
+                          ctypes.c_int),
+    "hd_serve_submit": ([_P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "hd_serve_poll": ([_P, ctypes.c_uint64, ctypes.POINTER(hd_result)], ctypes.c_int),
+    "hd_serve_release": ([_P, ctypes.c_uint64], ctypes.c_int),
+    "hd_serve_drain": ([_P], ctypes.c_int),
+    "hd_serve_completed": ([_P, _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)],
+                           ctypes.c_int),
+    "hd_serve_stats": ([_P, ctypes.POINTER(hd_serve_stats_t)], ctypes.c_int),
     "hd_version": ([], ctypes.c_char_p),
 }
 
@@ -320,6 +349,98 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self._lib.hd_launch_count(self.handle))
+
+
+class Server:
+    """A decode server (hd_serve_*): resident fields, requests admitted by a
+    device-memory budget, continuous batching over `slots` streams."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 40 << 30, slots: int = 2,
+                 max_batch: int = 64, queue_cap: int = 0, direct: bool = False,
+                 shape: Optional[dict] = None):
+        self._lib = load()
+        cfg = hd_serve_config(budget_bytes, slots, max_batch, queue_cap, 1 if direct else 0)
+        sh = None
+        if shape:
+            sh = hd_config(shape.get("subseq_bits", 0), shape.get("threads", 0),
+                           shape.get("window", 0), shape.get("lut_bits", 0))
+        h = ctypes.c_void_p()
+        _check("hd_serve_create", self._lib.hd_serve_create(
+            device, ctypes.byref(cfg), ctypes.byref(sh) if sh is not None else None,
+            ctypes.byref(h)))
+        self.handle = h
+        self._fields = []  # keeps the registered fields' tensors alive
+
+    def close(self):
+        if self.handle:
+            self._lib.hd_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def register(self, field: DeviceField) -> int:
+        fid = ctypes.c_uint32()
+        f = field.c_struct()
+        _check("hd_serve_register", self._lib.hd_serve_register(self.handle, ctypes.byref(f),
+                                                                ctypes.byref(fid)))
+        self._fields.append(field)
+        return fid.value
+
+    def submit(self, field_id: int) -> int:
+        t = ctypes.c_uint64()
+        _check("hd_serve_submit", self._lib.hd_serve_submit(self.handle, field_id,
+                                                            ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending, else a dict with status, d_out, n, queue_us, latency_us."""
+        r = hd_result()
+        rc = self._lib.hd_serve_poll(self.handle, ticket, ctypes.byref(r))
+        if rc == HD_PENDING:
+            return None
+        _check("hd_serve_poll", rc)
+        return {"status": r.status, "d_out": r.d_out, "n": r.n, "queue_us": r.queue_us,
+                "latency_us": r.latency_us}
+
+    def release(self, ticket: int) -> None:
+        _check("hd_serve_release", self._lib.hd_serve_release(self.handle, ticket))
+
+    def drain(self) -> None:
+        _check("hd_serve_drain", self._lib.hd_serve_drain(self.handle))
+
+    def completed(self, cap: int = 4096) -> np.ndarray:
+        """Tickets completed since the last call (uint64 array)."""
+        buf = np.empty(max(1, cap), dtype=np.uint64)
+        k = ctypes.c_uint32()
+        _check("hd_serve_completed", self._lib.hd_serve_completed(self.handle, _np_ptr(buf), cap,
+                                                                  ctypes.byref(k)))
+        return buf[:k.value]
+
+    def stats(self) -> dict:
+        s = hd_serve_stats_t()
+        _check("hd_serve_stats", self._lib.hd_serve_stats(self.handle, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in hd_serve_stats_t._fields_}
+
+
+class _DeviceSpan:
+    """A raw device range seen through the CUDA array interface (no copy)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i2", "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def device_u16_view(ptr: int, n: int, device: int = 0):
+    """The n uint16 symbols at a device pointer as an int16 torch tensor view
+    (valid while the memory is; clone() to keep them)."""
+    import torch
+    if n == 0:
+        return torch.empty(0, dtype=torch.int16, device=f"cuda:{device}")
+    return torch.as_tensor(_DeviceSpan(ptr, n), device=f"cuda:{device}")
 
 
 def hd_version() -> str:
