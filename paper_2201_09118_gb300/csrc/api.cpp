@@ -17,7 +17,7 @@
 
 // Cached graph: strategy, launch shape, capacities and workspace address.
 using GraphKey = std::tuple<bool, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t,
-                            uint64_t, size_t, uintptr_t>;
+                            uint32_t, uint64_t, size_t, uintptr_t>;
 // Autotuner class: strategy, mean code length in quarter bits, log2 of the
 // symbol count, largest stream subsequence size of the batch.
 using TuneKey = std::tuple<bool, uint32_t, uint32_t, uint32_t>;
@@ -199,7 +199,7 @@ uint64_t pow2_at_least(uint64_t v, uint64_t lo) {
 
 // Workspace layout of one launch; [0, zero) is cleared by the table kernel.
 struct Layout {
-  size_t err = 0, seg = 0, zero = 0, hdr = 0, desc = 0, tab = 0, tile = 0, count = 0;
+  size_t err = 0, zero = 0, hdr = 0, desc = 0, tab = 0, tile = 0, tbase = 0, count = 0;
   size_t gap = 0, ta = 0, te = 0, tf = 0, total = 0;
 };
 
@@ -209,8 +209,6 @@ Layout make_layout(uint32_t nf, uint64_t tiles, uint64_t subs, size_t tab_bytes,
   size_t off = 0;
   L.err = off;
   off = align_up(off + 4ull * nf, 16);
-  L.seg = off;  // codewords per 256 tiles
-  off = align_up(off + 8ull * ((tiles + 255) / 256 + 1), 16);
   L.zero = off;
   L.hdr = align_up(off, 256);  // launch header, then the field descriptors
   L.desc = L.hdr + 256;
@@ -219,6 +217,8 @@ Layout make_layout(uint32_t nf, uint64_t tiles, uint64_t subs, size_t tab_bytes,
   off = L.tab + tab_bytes;
   L.tile = align_up(off, 256);
   off = L.tile + 4ull * tiles;
+  L.tbase = align_up(off, 256);  // exclusive scan of the tile totals
+  off = L.tbase + 8ull * (tiles + 1);
   L.count = align_up(off, 256);
   off = L.count + hd::count_bytes_per_subsequence(s.S) * subs;
   // self-synchronisation: subsequence starts, tile links (16-byte padded)
@@ -255,6 +255,8 @@ int prepare_launch(const hd_ctx* c, std::vector<FieldDesc>& descs, const hd::Lau
   const double bits_per = static_cast<double>(bits) / static_cast<double>(syms ? syms : 1);
   // symbols of codes longer than the first-level table, kept in shared memory
   s.long_cap = static_cast<uint32_t>(align_up(std::min<uint32_t>(amax, 4096), 8));
+  // 16-bit first-level entries when every field's symbols fit 12 bits
+  s.lut16 = hd::lut16_usable(s.K, amax) ? 1u : 0u;
   if (s.window == 0) {
     // output window: about 1.2x a tile's expected symbol count, rounded up to
     // a multiple of 2048 so that batches of similar code lengths share a shape
@@ -330,7 +332,7 @@ void make_params(const std::vector<FieldDesc>& descs, char* ws, const Layout& L,
   dp.total_units = tiles_param;
   dp.counts = ws + L.count;
   dp.tile_total = reinterpret_cast<uint32_t*>(ws + L.tile);
-  dp.seg_total = reinterpret_cast<uint64_t*>(ws + L.seg);
+  dp.tile_base = reinterpret_cast<uint64_t*>(ws + L.tbase);
   if (self_sync) {
     dp.tile_a = reinterpret_cast<uint8_t*>(ws + L.ta);
     dp.tile_e = reinterpret_cast<uint8_t*>(ws + L.te);
@@ -339,10 +341,12 @@ void make_params(const std::vector<FieldDesc>& descs, char* ws, const Layout& L,
 }
 
 // The kernels of one strategy, in stream order:
-//   gap array            table kernel, count kernel, decode-and-write kernel;
+//   gap array            table kernel, count kernel, tile scan, decode-and-write
+//                        kernel;
 //   self-synchronisation table kernel, synchronising kernel, link-fix kernel,
-//                        then the same decode-and-write kernel (with sync_only
-//                        the last is left out: the starts stay in each gap_out).
+//                        then the same tile scan and decode-and-write kernel
+//                        (with sync_only the last two are left out: the starts
+//                        stay in each gap_out).
 cudaError_t launch_all(const hd_ctx* c, const hd::PrepParams& pp, const hd::DecodeParams& dp,
                        const hd::LaunchShape& s, bool self_sync, bool sync_only,
                        cudaStream_t st) {
@@ -357,7 +361,7 @@ cudaError_t launch_all(const hd_ctx* c, const hd::PrepParams& pp, const hd::Deco
 }
 
 uint32_t kernels_per_launch(bool self_sync, bool sync_only) {
-  return self_sync ? (sync_only ? 3u : 4u) : 3u;
+  return self_sync ? (sync_only ? 3u : 5u) : 4u;
 }
 
 // Queues a decode of fields that all use the same strategy with direct
@@ -456,8 +460,8 @@ int queue_decode_graph(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::Launc
     return HD_ERR_CUDA;
   c->pinned_busy = true;
 
-  const GraphKey key{self_sync, P.s.S, P.s.threads, P.s.K, P.s.window, P.s.long_cap,
-                     cap_f, cap_t, cap_tab, reinterpret_cast<uintptr_t>(ws)};
+  const GraphKey key{self_sync, P.s.S,     P.s.threads, P.s.K, P.s.window, P.s.long_cap,
+                     P.s.lut16, cap_f,       cap_t, cap_tab,    reinterpret_cast<uintptr_t>(ws)};
   auto it = c->graphs.find(key);
   cudaGraphExec_t exec = nullptr;
   if (it != c->graphs.end()) {

@@ -9,9 +9,11 @@ namespace hd {
 constexpr uint32_t kMaxCodeLen = 32;
 constexpr uint32_t kTableHeaderBytes = 512;
 
-// Decode-table header, written by the table kernel, followed in memory by the
-// first-level table (uint32[2^K]) at kTableHeaderBytes and then by the symbols
-// sorted by (code length, symbol) (uint16[alphabet]).
+// Decode-table header, written by the table kernel.  A decode table is, in
+// order: the header (kTableHeaderBytes), the 32-bit first-level table
+// (uint32[2^K]), the symbols sorted by (code length, symbol) (uint16[A]), the
+// 16-bit first-level table (uint16[2^K], only when A <= 4096 and K <= 15) and
+// the first-level length table (uint8[2^K]); offsets below.
 //
 // Canonical codes occupy, for each length L, the left-aligned 32-bit interval
 //   [first[L] << (32-L), (first[L] + count[L]) << (32-L)),
@@ -32,8 +34,36 @@ static_assert(sizeof(TableHeader) <= kTableHeaderBytes, "table header too large"
 // First-level entry: bit 31 clear -> (len << 16) | symbol with len <= K;
 // bit 31 set -> the code is longer than K bits (or the prefix is no code):
 // bits 0..7 hold the smallest length a code with this prefix can have (33 if
-// none can), and the length is found by walking end[] from there.
+// none can), bits 8..15 the largest when every window with this prefix is a
+// valid code (else 0xFF).  Canonical lengths grow with the window value, so
+// when the two are equal every code under the prefix has that length;
+// otherwise the length is found by walking end[] from the smallest.
 constexpr uint32_t kLongFlag = 0x80000000u;
+
+// 16-bit first-level entry (alphabets up to 4096, K <= 15): bits 12..15 hold
+// the length (1..15) and bits 0..11 the symbol of a code of at most K bits;
+// length 0 marks a longer code (or no code): bits 0..7 then hold the smallest
+// length under the prefix and bit 11 is set when the prefix holds codes of
+// several lengths (the length is then found by walking end[]).
+constexpr uint32_t kLut16Mixed = 0x800u;
+
+// 8-bit first-level length entry: the code length when every code under the
+// prefix has the same length (this includes all codes of at most K bits);
+// else 0x80 | the smallest length under the prefix (33: no code).
+constexpr uint32_t kLen8Walk = 0x80u;
+
+__host__ __device__ constexpr uint64_t table_sorted_off(uint32_t K) {
+  return kTableHeaderBytes + (static_cast<uint64_t>(4) << K);
+}
+__host__ __device__ constexpr uint64_t table_lut16_off(uint32_t K, uint32_t A) {
+  return (table_sorted_off(K) + 2ull * A + 15) & ~static_cast<uint64_t>(15);
+}
+__host__ __device__ constexpr uint64_t table_len8_off(uint32_t K, uint32_t A) {
+  return table_lut16_off(K, A) + (static_cast<uint64_t>(2) << K);
+}
+__host__ __device__ constexpr bool lut16_usable(uint32_t K, uint32_t A) {
+  return A <= 4096 && K <= 15;
+}
 
 // Per-field work description (device memory for batches, a kernel parameter
 // for single fields).
@@ -92,7 +122,7 @@ struct DecodeParams {
   uint64_t timeout_cycles;  // per-wait limit in SM clock cycles
   void* counts;             // two-phase decode: codewords per subsequence (u8, or u16 for S=256)
   uint32_t* tile_total;     // two-phase decode: codewords per tile
-  uint64_t* seg_total;      // two-phase decode: codewords per 256 tiles (zeroed before launch)
+  uint64_t* tile_base;      // exclusive scan of tile_total over the launch ([units + 1])
   uint8_t* tile_a;          // self-synchronisation: start offset each tile assumed
   uint8_t* tile_e;          // self-synchronisation: tile_e[g + 1] = where tile g stopped, minus S
   uint8_t* tile_flag;       // self-synchronisation: 1 = last subsequence overran nbits

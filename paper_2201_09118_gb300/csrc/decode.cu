@@ -152,20 +152,12 @@ __global__ void __launch_bounds__(B) k_decode(const __grid_constant__ DecodePara
     const uint32_t fi = s_field;
     const FieldDesc& F = field_of(P, LS, fi);
     if (fi != cur_field) {
-      load_table(F.table, P.K, s_lut, s_end, s_base, s_meta, B, s_long, P.long_cap);
+      load_table(F.table, P.K, F.alphabet, Lut::k32, s_lut, s_end, s_base, s_meta, B, s_long,
+                 P.long_cap);
       cur_field = fi;
       __syncthreads();
     }
-    const Tables T{s_lut,
-                   s_end,
-                   s_base,
-                   reinterpret_cast<const uint16_t*>(reinterpret_cast<const char*>(F.table) +
-                                                     kTableHeaderBytes + (4u << P.K)),
-                   s_long,
-                   s_meta[2],
-                   P.long_cap,
-                   s_meta[0],
-                   32u - P.K};
+    const Tables T = make_tables(F, P.K, s_lut, s_end, s_base, s_meta, s_long, P.long_cap);
     const bool table_ok = s_meta[1] == 0;
 
     const uint64_t tl = g - F.unit_begin;

@@ -5,19 +5,20 @@
 // subsequence, a prefix sum turns the counts into output indices (Sec. III-B2
 // step 3), and a decode-and-write pass stages each block's symbols in a
 // shared-memory window and writes them with coalesced stores (Algorithm 1,
-// Sec. IV-B).  On GB300 both passes are persistent, look-back-free kernels:
+// Sec. IV-B).  On GB300 the passes are persistent, look-back-free kernels:
 //
 //   k_count   every thread counts the codewords of one subsequence (start from
 //             the gap array, bits staged in shared memory, decode-table lookups
 //             for the lengths), checks that it ends where the next subsequence
-//             starts, stores the count, and each tile adds its total to a
-//             per-tile array and to the total of its 256-tile segment.
-//   k_write   a warp sums the segment totals and tile totals before its tile
-//             (one parallel round of loads), the block scans the per-thread
-//             counts, and every thread decodes its subsequence straight into
-//             the window at its output offset; the window is then written out.
+//             starts and stores the count; each tile stores its total.
+//   k_scan    one block turns the tile totals of the launch into exclusive
+//             tile bases (a device-wide scan over tiles).
+//   k_write   the block scans its per-thread counts and every thread decodes
+//             its subsequence straight into the window at its output offset
+//             (tile base from k_scan); the window is then written out.
 //
-// Tiles are B subsequences of S bits.
+// Tiles are B subsequences of S bits.  Blocks load the next tile's bits, gap
+// entries and counts into registers while they decode the current tile.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -42,8 +43,6 @@ struct CountType<512> {
   using T = uint16_t;
 };
 
-constexpr int kSegTiles = 256;
-
 // Block-wide sum (all B threads); ends with a barrier.
 template <int B>
 __device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* s_warp) {
@@ -60,14 +59,47 @@ __device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* s_warp) {
   return tot;
 }
 
+// What a thread needs of its subsequence of one tile, loaded ahead.
+template <int S>
+struct TileIn {
+  UnitRegs<S> bits;
+  uint32_t gap0, gap1;  // gap entries of this and the next subsequence
+  uint32_t count;       // k_write: the subsequence's codeword count
+  uint64_t base;        // k_write: the tile's first output index (thread 0)
+};
+
+template <int S, int B, bool WRITE>
+__device__ __forceinline__ void fetch_tile(TileIn<S>& in, const DecodeParams& P,
+                                           const FieldDesc& F, uint64_t g) {
+  using CT = typename CountType<S>::T;
+  const uint64_t i = (g - F.unit_begin) * B + threadIdx.x;
+  if (i < F.nsub) {
+    fetch_units<S>(in.bits, F, i);
+    in.gap0 = __ldg(F.gap + i * F.gap_stride);
+    in.gap1 = (i + 1 < F.nsub) ? __ldg(F.gap + (i + 1) * F.gap_stride) : 0u;
+    if (WRITE) in.count = reinterpret_cast<const CT*>(P.counts)[F.count_begin + i];
+  }
+  if (WRITE && threadIdx.x == 0) in.base = P.tile_base[g] - P.tile_base[F.unit_begin];
+}
+
+// Register caps that keep 4 blocks of 256 threads per SM.
+template <int B>
+__host__ __device__ constexpr int count_min_blocks() {
+  return 1024 / B;
+}
+template <int B>
+__host__ __device__ constexpr int write_min_blocks() {
+  return 1024 / B;
+}
+
 template <int S, int B>
-__global__ void __launch_bounds__(B) k_count(const __grid_constant__ DecodeParams P) {
+__global__ void __launch_bounds__(B, count_min_blocks<B>())
+    k_count(const __grid_constant__ DecodeParams P) {
   using CT = typename CountType<S>::T;
   constexpr int W = S / 32 + 1;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* s_lut = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* s_bits = s_lut + (1u << P.K);
-  uint16_t* s_long = reinterpret_cast<uint16_t*>(s_bits + W * B);
+  uint8_t* s_lut = smem;  // length table
+  uint32_t* s_bits = reinterpret_cast<uint32_t*>(smem + lut_bytes(Lut::k8, P.K));
   __shared__ uint64_t s_end[34];
   __shared__ uint32_t s_base[34];
   __shared__ uint32_t s_meta[3];
@@ -77,43 +109,48 @@ __global__ void __launch_bounds__(B) k_count(const __grid_constant__ DecodeParam
   uint32_t* col = s_bits + t;
   uint32_t cur_field = 0xffffffffu;
   const LaunchSize LS = launch_size(P);
-  for (uint64_t g = blockIdx.x; g < LS.units; g += gridDim.x) {
-    const uint32_t fi = find_field(P, LS, g);
+  uint64_t g = blockIdx.x;
+  TileIn<S> nxt;
+  uint32_t nfi = 0;
+  if (g < LS.units) {
+    nfi = find_field(P, LS, g);
+    fetch_tile<S, B, false>(nxt, P, field_of(P, LS, nfi), g);
+  }
+  for (; g < LS.units; g += gridDim.x) {
+    const uint32_t fi = nfi;
     const FieldDesc& F = field_of(P, LS, fi);
+    // this tile's bits go to shared memory (each thread touches only its own
+    // column), then the registers take the next tile's loads
+    const uint64_t i = (g - F.unit_begin) * B + t;
+    if (i < F.nsub) put_units<S>(col, nxt.bits, B);
+    const uint32_t gap0 = nxt.gap0, gap1 = nxt.gap1;
+    const uint64_t gn = g + gridDim.x;
+    if (gn < LS.units) {
+      nfi = find_field(P, LS, gn);
+      fetch_tile<S, B, false>(nxt, P, field_of(P, LS, nfi), gn);
+    }
     if (fi != cur_field) {
       __syncthreads();
-      load_table(F.table, P.K, s_lut, s_end, s_base, s_meta, B, s_long, P.long_cap);
+      load_table(F.table, P.K, F.alphabet, Lut::k8, s_lut, s_end, s_base, s_meta, B);
       cur_field = fi;
       __syncthreads();
     }
-    const Tables T{s_lut,
-                   s_end,
-                   s_base,
-                   reinterpret_cast<const uint16_t*>(reinterpret_cast<const char*>(F.table) +
-                                                     kTableHeaderBytes + (4u << P.K)),
-                   s_long,
-                   s_meta[2],
-                   P.long_cap,
-                   s_meta[0],
-                   32u - P.K};
+    const Tables T = make_tables(F, P.K, s_lut, s_end, s_base, s_meta, nullptr, 0);
     const bool table_ok = s_meta[1] == 0;
     const uint64_t tl = g - F.unit_begin;
-    const uint64_t i = tl * B + t;
     uint32_t c = 0, err = 0;
     if (table_ok && i < F.nsub) {
-      stage_units<S>(col, F, i, B);
       const uint64_t rem = F.nbits - i * S;
       const uint32_t end = rem < S ? static_cast<uint32_t>(rem) : S;
-      uint32_t p = F.gap[i * F.gap_stride];
-      const uint32_t expect =
-          (i + 1 < F.nsub) ? S + F.gap[(i + 1) * F.gap_stride] : static_cast<uint32_t>(rem);
+      uint32_t p = gap0;
+      const uint32_t expect = (i + 1 < F.nsub) ? S + gap1 : static_cast<uint32_t>(rem);
       if (p > end || p >= S) {
         err |= kErrGap;
         p = end;
       }
       bool bad = false;
       while (p < end) {
-        p += code_len(T, peek<B>(col, p), bad);
+        p += code_len8(T, peek<B>(col, p), bad);
         ++c;
       }
       if (bad) err |= kErrCode;
@@ -123,41 +160,60 @@ __global__ void __launch_bounds__(B) k_count(const __grid_constant__ DecodeParam
     if (err) atomicOr(F.err, err);
     if (t == 0 && !table_ok && tl == 0) atomicOr(F.err, kErrTable);
     const uint32_t C = block_sum<B>(c, s_warp);
-    if (t == 0) {
-      P.tile_total[g] = C;
-      atomicAdd(reinterpret_cast<unsigned long long*>(P.seg_total + g / kSegTiles),
-                static_cast<unsigned long long>(C));
-    }
+    if (t == 0) P.tile_total[g] = C;
   }
 }
 
-// Warp: sum of the counts of tiles [a, b) (all of one field).  Whole 256-tile
-// segments inside the range come from the segment totals, the ragged ends
-// from the tile totals; every lane issues its loads at once.
-__device__ __forceinline__ uint64_t tiles_prefix(const DecodeParams& P, uint64_t a, uint64_t b) {
-  const int lane = threadIdx.x & 31;
+// One block of kScanThreads: tile_base[g] = sum of tile_total[j] for j < g,
+// over all tiles of the launch (g in [0, units]).  Each thread owns a
+// contiguous run of tiles.
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ DecodeParams P) {
+  __shared__ uint64_t s_part[kScanThreads / 32];
+  const LaunchSize LS = launch_size(P);
+  const uint64_t n = LS.units;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const uint64_t per = (n + kScanThreads - 1) / kScanThreads;
+  const uint64_t a = per * t < n ? per * t : n;
+  const uint64_t b = a + per < n ? a + per : n;
   uint64_t sum = 0;
-  if (b > a) {
-    const uint64_t s0 = (a + kSegTiles - 1) / kSegTiles;  // first whole segment
-    const uint64_t s1 = b / kSegTiles;                    // end of whole segments
-    if (s0 < s1) {
-      for (uint64_t j = a + lane; j < s0 * kSegTiles; j += 32) sum += P.tile_total[j];
-      for (uint64_t s = s0 + lane; s < s1; s += 32) sum += P.seg_total[s];
-      for (uint64_t j = s1 * kSegTiles + lane; j < b; j += 32) sum += P.tile_total[j];
-    } else {
-      for (uint64_t j = a + lane; j < b; j += 32) sum += P.tile_total[j];
-    }
+  for (uint64_t j = a; j < b; ++j) sum += P.tile_total[j];
+  // exclusive block scan of the per-thread sums
+  uint64_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
   }
-  return warp_sum_u64(sum);
+  if (lane == 31) s_part[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t v = s_part[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    s_part[lane] = v;
+  }
+  __syncthreads();
+  uint64_t run = (warp ? s_part[warp - 1] : 0ull) + incl - sum;
+  for (uint64_t j = a; j < b; ++j) {
+    P.tile_base[j] = run;
+    run += P.tile_total[j];
+  }
+  if (t == kScanThreads - 1) P.tile_base[n] = s_part[kScanThreads / 32 - 1];
 }
 
-template <int S, int B>
-__global__ void __launch_bounds__(B) k_write(const __grid_constant__ DecodeParams P) {
-  using CT = typename CountType<S>::T;
+template <int S, int B, class E>
+__global__ void __launch_bounds__(B, write_min_blocks<B>())
+    k_write(const __grid_constant__ DecodeParams P) {
   constexpr int W = S / 32 + 1;
+  constexpr Lut kKind = sizeof(E) == 2 ? Lut::k16 : Lut::k32;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* s_lut = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* s_bits = s_lut + (1u << P.K);
+  unsigned char* s_lut = smem;
+  uint32_t* s_bits = reinterpret_cast<uint32_t*>(smem + lut_bytes(kKind, P.K));
   uint16_t* s_out = reinterpret_cast<uint16_t*>(s_bits + W * B);  // window + 16
   uint16_t* s_long = s_out + P.window + 16;
   __shared__ uint64_t s_end[34];
@@ -168,42 +224,43 @@ __global__ void __launch_bounds__(B) k_write(const __grid_constant__ DecodeParam
   __shared__ uint32_t s_flush_end;
 
   const int t = threadIdx.x;
-  const int warp = t >> 5;
   uint32_t* col = s_bits + t;
   uint32_t cur_field = 0xffffffffu;
   const LaunchSize LS = launch_size(P);
-  for (uint64_t g = blockIdx.x; g < LS.units; g += gridDim.x) {
-    const uint32_t fi = find_field(P, LS, g);
+  uint64_t g = blockIdx.x;
+  TileIn<S> nxt;
+  uint32_t nfi = 0;
+  if (g < LS.units) {
+    nfi = find_field(P, LS, g);
+    fetch_tile<S, B, true>(nxt, P, field_of(P, LS, nfi), g);
+  }
+  for (; g < LS.units; g += gridDim.x) {
+    const uint32_t fi = nfi;
     const FieldDesc& F = field_of(P, LS, fi);
+    const uint64_t i = (g - F.unit_begin) * B + t;
+    if (i < F.nsub) put_units<S>(col, nxt.bits, B);
+    const uint32_t gap0 = nxt.gap0, count0 = nxt.count;
+    if (t == 0) s_tile_base = nxt.base;
+    const uint64_t gn = g + gridDim.x;
+    if (gn < LS.units) {
+      nfi = find_field(P, LS, gn);
+      fetch_tile<S, B, true>(nxt, P, field_of(P, LS, nfi), gn);
+    }
     if (fi != cur_field) {
       __syncthreads();
-      load_table(F.table, P.K, s_lut, s_end, s_base, s_meta, B, s_long, P.long_cap);
+      load_table(F.table, P.K, F.alphabet, kKind, s_lut, s_end, s_base, s_meta, B, s_long,
+                 P.long_cap);
       cur_field = fi;
       __syncthreads();
     }
-    const Tables T{s_lut,
-                   s_end,
-                   s_base,
-                   reinterpret_cast<const uint16_t*>(reinterpret_cast<const char*>(F.table) +
-                                                     kTableHeaderBytes + (4u << P.K)),
-                   s_long,
-                   s_meta[2],
-                   P.long_cap,
-                   s_meta[0],
-                   32u - P.K};
+    const Tables T = make_tables(F, P.K, s_lut, s_end, s_base, s_meta, s_long, P.long_cap);
     const bool table_ok = s_meta[1] == 0;
     const uint64_t tl = g - F.unit_begin;
-    const uint64_t i = tl * B + t;
     const bool valid = table_ok && i < F.nsub;
     uint32_t c = 0, gp = 0;
-    if (warp == 0) {
-      const uint64_t base = tiles_prefix(P, F.unit_begin, g);
-      if (t == 0) s_tile_base = base;
-    }
     if (valid) {
-      c = reinterpret_cast<const CT*>(P.counts)[F.count_begin + i];
-      gp = min(static_cast<uint32_t>(F.gap[i * F.gap_stride]), static_cast<uint32_t>(S));
-      stage_units<S>(col, F, i, B);
+      c = count0;
+      gp = min(gap0, static_cast<uint32_t>(S));
     }
     uint32_t C;
     const uint32_t o = block_excl_scan<B>(c, s_warp, &C);
@@ -215,7 +272,7 @@ __global__ void __launch_bounds__(B) k_write(const __grid_constant__ DecodeParam
                       bool bad = false;
                       for (uint32_t j = 0; j < c; ++j) {
                         uint32_t sym;
-                        p += code_sym(T, peek<B>(col, p), sym, bad);
+                        p += code_sym_t<E>(T, peek<B>(col, p), sym, bad);
                         dst[j] = static_cast<uint16_t>(sym);
                       }
                       if (bad) atomicOr(F.err, kErrCode);
@@ -241,17 +298,30 @@ cudaError_t launch_persistent(Kern kern, const DecodeParams& p, int B, size_t sm
   return cudaGetLastError();
 }
 
+cudaError_t launch_scan(const DecodeParams& p, cudaStream_t stream) {
+  k_scan<<<1, kScanThreads, 0, stream>>>(p);
+  return cudaGetLastError();
+}
+
+template <int S, int B>
+cudaError_t launch_write_sb(const DecodeParams& p, const LaunchShape& s, int num_sms,
+                            cudaStream_t stream) {
+  if (s.lut16)
+    return launch_persistent(k_write<S, B, uint16_t>, p, B, two_phase_smem_bytes(s), num_sms,
+                             s.grid, stream);
+  return launch_persistent(k_write<S, B, uint32_t>, p, B, two_phase_smem_bytes(s), num_sms,
+                           s.grid, stream);
+}
+
 template <int S, int B>
 cudaError_t launch_sb(const DecodeParams& p, const LaunchShape& s, int num_sms,
                       cudaStream_t stream) {
-  const size_t W = S / 32 + 1;
-  const size_t lut = (static_cast<size_t>(1) << s.K) * 4;
-  const size_t smem_count = ((lut + W * B * 4 + s.long_cap * 2) + 15) & ~static_cast<size_t>(15);
   cudaError_t e =
-      launch_persistent(k_count<S, B>, p, B, smem_count, num_sms, s.grid, stream);
+      launch_persistent(k_count<S, B>, p, B, count_smem_bytes(s), num_sms, s.grid, stream);
   if (e != cudaSuccess) return e;
-  return launch_persistent(k_write<S, B>, p, B, two_phase_smem_bytes(s), num_sms, s.grid,
-                           stream);
+  e = launch_scan(p, stream);
+  if (e != cudaSuccess) return e;
+  return launch_write_sb<S, B>(p, s, num_sms, stream);
 }
 
 template <int S>
@@ -268,11 +338,12 @@ cudaError_t launch_s(const DecodeParams& p, const LaunchShape& s, int num_sms,
 template <int S>
 cudaError_t launch_write_s(const DecodeParams& p, const LaunchShape& s, int num_sms,
                            cudaStream_t stream) {
-  const size_t smem = two_phase_smem_bytes(s);
+  cudaError_t e = launch_scan(p, stream);
+  if (e != cudaSuccess) return e;
   switch (s.threads) {
-    case 128: return launch_persistent(k_write<S, 128>, p, 128, smem, num_sms, s.grid, stream);
-    case 256: return launch_persistent(k_write<S, 256>, p, 256, smem, num_sms, s.grid, stream);
-    case 512: return launch_persistent(k_write<S, 512>, p, 512, smem, num_sms, s.grid, stream);
+    case 128: return launch_write_sb<S, 128>(p, s, num_sms, stream);
+    case 256: return launch_write_sb<S, 256>(p, s, num_sms, stream);
+    case 512: return launch_write_sb<S, 512>(p, s, num_sms, stream);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -281,9 +352,15 @@ cudaError_t launch_write_s(const DecodeParams& p, const LaunchShape& s, int num_
 
 size_t two_phase_smem_bytes(const LaunchShape& s) {
   const size_t W = s.S / 32 + 1;
-  size_t b = (static_cast<size_t>(1) << s.K) * 4 + W * s.threads * 4;
+  size_t b = dev::lut_bytes(s.lut16 ? dev::Lut::k16 : dev::Lut::k32, s.K) + W * s.threads * 4;
   b += (static_cast<size_t>(s.window) + 16) * 2;
   b += static_cast<size_t>(s.long_cap) * 2;
+  return (b + 15) & ~static_cast<size_t>(15);
+}
+
+size_t count_smem_bytes(const LaunchShape& s) {
+  const size_t W = s.S / 32 + 1;
+  const size_t b = dev::lut_bytes(dev::Lut::k8, s.K) + W * s.threads * 4;
   return (b + 15) & ~static_cast<size_t>(15);
 }
 

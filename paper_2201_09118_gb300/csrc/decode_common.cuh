@@ -35,11 +35,12 @@ __device__ __forceinline__ uint2 ldg_v2(const uint32_t* p) {
   return __ldg(reinterpret_cast<const uint2*>(p));
 }
 
-// Decode tables as seen by one block: first level in shared memory, the
-// per-length limits in shared memory, the sorted symbols in global memory
-// (only codes longer than K bits read them).
+// Decode tables as seen by one block: one first-level table in shared memory
+// (32-bit, 16-bit or length entries, see common.cuh), the per-length limits in
+// shared memory, the sorted symbols in global memory (only codes longer than
+// K bits read them) with the first long_cap long-code symbols in shared memory.
 struct Tables {
-  const uint32_t* lut;
+  const void* lut;
   const uint64_t* end;
   const uint32_t* base;
   const uint16_t* sorted;    // all symbols by (length, symbol), global memory
@@ -59,40 +60,94 @@ __device__ __forceinline__ uint32_t peek(const uint32_t* col, uint32_t p) {
   return __funnelshift_l(col[(k + 1) * B], col[k * B], p);
 }
 
-// Length of the codeword at window w (long codes walk the canonical limits).
-// An invalid bit pattern sets `bad` and counts as one bit, so a decoder that
-// started at a wrong position still advances.
-__device__ __forceinline__ uint32_t code_len(const Tables& T, uint32_t w, bool& bad) {
-  const uint32_t e = T.lut[w >> T.shift];
-  if (!(e & kLongFlag)) return e >> 16;
-  uint32_t L = e & 0xFFu;
+// The length of the code at window w when the first-level entry only gave a
+// lower bound L: walk the canonical limits.  An invalid bit pattern sets `bad`
+// and counts as one bit, so a decoder that started at a wrong position still
+// advances.
+__device__ __forceinline__ uint32_t walk_len(const Tables& T, uint32_t w, uint32_t L, bool& bad) {
   while (L <= T.maxlen && static_cast<uint64_t>(w) >= T.end[L]) ++L;
   if (L > T.maxlen) {
     bad = true;
-    return 1;
+    return 0;
   }
   return L;
 }
 
-// Length and symbol of the codeword at window w.
+// Symbol of a code longer than the first-level table.
+__device__ __forceinline__ uint32_t long_sym(const Tables& T, uint32_t w, uint32_t L) {
+  const uint32_t rank = (w >> (32 - L)) + T.base[L];
+  const uint32_t li = rank - T.long0;
+  return li < T.long_cap ? T.long_syms[li] : __ldg(T.sorted + rank);
+}
+
+// Length of the codeword at window w from the 32-bit table.
+__device__ __forceinline__ uint32_t code_len(const Tables& T, uint32_t w, bool& bad) {
+  const uint32_t e = static_cast<const uint32_t*>(T.lut)[w >> T.shift];
+  if (!(e & kLongFlag)) return e >> 16;
+  const uint32_t L = e & 0xFFu;
+  if (L == ((e >> 8) & 0xFFu)) return L;  // one length under this prefix
+  const uint32_t Lw = walk_len(T, w, L, bad);
+  return Lw ? Lw : 1u;
+}
+
+// Length of the codeword at window w from the length table.
+__device__ __forceinline__ uint32_t code_len8(const Tables& T, uint32_t w, bool& bad) {
+  const uint32_t e = static_cast<const uint8_t*>(T.lut)[w >> T.shift];
+  if (!(e & kLen8Walk)) return e;
+  const uint32_t Lw = walk_len(T, w, e & 0x7Fu, bad);
+  return Lw ? Lw : 1u;
+}
+
+// Length and symbol of the codeword at window w from the 32-bit table.
 __device__ __forceinline__ uint32_t code_sym(const Tables& T, uint32_t w, uint32_t& sym,
                                              bool& bad) {
-  const uint32_t e = T.lut[w >> T.shift];
+  const uint32_t e = static_cast<const uint32_t*>(T.lut)[w >> T.shift];
   if (!(e & kLongFlag)) {
     sym = e & 0xFFFFu;
     return e >> 16;
   }
   uint32_t L = e & 0xFFu;
-  while (L <= T.maxlen && static_cast<uint64_t>(w) >= T.end[L]) ++L;
-  if (L > T.maxlen) {
-    bad = true;
-    sym = 0;
-    return 1;
+  if (L != ((e >> 8) & 0xFFu)) {
+    L = walk_len(T, w, L, bad);
+    if (!L) {
+      sym = 0;
+      return 1;
+    }
   }
-  const uint32_t rank = (w >> (32 - L)) + T.base[L];
-  const uint32_t li = rank - T.long0;
-  sym = li < T.long_cap ? T.long_syms[li] : __ldg(T.sorted + rank);
+  sym = long_sym(T, w, L);
   return L;
+}
+
+// Length and symbol of the codeword at window w from the 16-bit table.
+__device__ __forceinline__ uint32_t code_sym16(const Tables& T, uint32_t w, uint32_t& sym,
+                                               bool& bad) {
+  const uint32_t e = static_cast<const uint16_t*>(T.lut)[w >> T.shift];
+  uint32_t L = e >> 12;
+  if (L) {
+    sym = e & 0xFFFu;
+    return L;
+  }
+  L = e & 0xFFu;
+  if (e & kLut16Mixed) {
+    L = walk_len(T, w, L, bad);
+    if (!L) {
+      sym = 0;
+      return 1;
+    }
+  }
+  sym = long_sym(T, w, L);
+  return L;
+}
+
+// Entry type of the symbol table: E = uint32_t or uint16_t.
+template <class E>
+__device__ __forceinline__ uint32_t code_sym_t(const Tables& T, uint32_t w, uint32_t& sym,
+                                               bool& bad) {
+  if constexpr (sizeof(E) == 2) {
+    return code_sym16(T, w, sym, bad);
+  } else {
+    return code_sym(T, w, sym, bad);
+  }
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
@@ -197,18 +252,29 @@ __device__ __forceinline__ void window_write(uint16_t* s_out, uint32_t* s_flush_
   }
 }
 
+// Which first-level table a kernel keeps in shared memory.
+enum class Lut { k32, k16, k8 };
+
+__host__ __device__ constexpr uint32_t lut_bytes(Lut kind, uint32_t K) {
+  return kind == Lut::k32 ? (4u << K) : kind == Lut::k16 ? (2u << K) : (1u << K);
+}
+
 // Loads the decode table of a field into shared memory (threads [0, nthreads)):
-// the first-level table, the per-length limits and the first long_cap symbols
-// of codes longer than K.  s_meta = {maxlen, status, long0}.
-__device__ __forceinline__ void load_table(const TableHeader* H, uint32_t K, uint32_t* s_lut,
-                                           uint64_t* s_end, uint32_t* s_base,
-                                           uint32_t* s_meta, int nthreads,
+// the chosen first-level table (s_lut, 16-byte aligned), the per-length limits
+// and the first long_cap symbols of codes longer than K.
+// s_meta = {maxlen, status, long0}.
+__device__ __forceinline__ void load_table(const TableHeader* H, uint32_t K, uint32_t alphabet,
+                                           Lut kind, void* s_lut, uint64_t* s_end,
+                                           uint32_t* s_base, uint32_t* s_meta, int nthreads,
                                            uint16_t* s_long = nullptr, uint32_t long_cap = 0) {
   const int t = threadIdx.x;
-  const uint4* src =
-      reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(H) + kTableHeaderBytes);
+  const char* tb = reinterpret_cast<const char*>(H);
+  const uint64_t off = kind == Lut::k32   ? kTableHeaderBytes
+                       : kind == Lut::k16 ? table_lut16_off(K, alphabet)
+                                          : table_len8_off(K, alphabet);
+  const uint4* src = reinterpret_cast<const uint4*>(tb + off);
   uint4* dst = reinterpret_cast<uint4*>(s_lut);
-  const uint32_t nv = (1u << K) / 4;
+  const uint32_t nv = lut_bytes(kind, K) / 16;
   for (uint32_t k = t; k < nv; k += nthreads) dst[k] = __ldg(src + k);
   if (t < 34) {
     s_end[t] = H->end[t];
@@ -220,12 +286,28 @@ __device__ __forceinline__ void load_table(const TableHeader* H, uint32_t K, uin
     s_meta[2] = H->long0;
   }
   if (long_cap) {
-    const uint16_t* sorted = reinterpret_cast<const uint16_t*>(
-        reinterpret_cast<const char*>(H) + kTableHeaderBytes + (4u << K));
+    const uint16_t* sorted = reinterpret_cast<const uint16_t*>(tb + table_sorted_off(K));
     const uint32_t nused = H->nused, l0 = H->long0;
     const uint32_t nl = nused > l0 ? nused - l0 : 0u;
     for (uint32_t k = t; k < long_cap; k += nthreads) s_long[k] = k < nl ? sorted[l0 + k] : 0;
   }
+}
+
+// The Tables view of a loaded table.
+__device__ __forceinline__ Tables make_tables(const FieldDesc& F, uint32_t K, const void* s_lut,
+                                              const uint64_t* s_end, const uint32_t* s_base,
+                                              const uint32_t* s_meta, const uint16_t* s_long,
+                                              uint32_t long_cap) {
+  return Tables{s_lut,
+                s_end,
+                s_base,
+                reinterpret_cast<const uint16_t*>(reinterpret_cast<const char*>(F.table) +
+                                                  table_sorted_off(K)),
+                s_long,
+                s_meta[2],
+                long_cap,
+                s_meta[0],
+                32u - K};
 }
 
 // Field and tile counts of this launch (kernel parameters, or the device-side
@@ -288,6 +370,49 @@ __device__ __forceinline__ void stage_units(uint32_t* col, const FieldDesc& F, u
     for (int k = 0; k < U; ++k) col[k * stride] = (w0 + k < F.nwords) ? __ldg(src + k) : 0u;
   }
   col[U * stride] = (w0 + U < F.nwords) ? __ldg(src + U) : 0u;
+}
+
+// The units of one subsequence held in registers, so that a tile's loads can
+// be issued while the previous tile is still being decoded.
+template <int S>
+struct UnitRegs {
+  uint32_t u[S / 32 + 1];
+};
+
+// Loads subsequence i (its S/32 units and the following one) of field F;
+// units past the readable stream read as zero.
+template <int S>
+__device__ __forceinline__ void fetch_units(UnitRegs<S>& r, const FieldDesc& F, uint64_t i) {
+  constexpr int U = S / 32;
+  const uint64_t w0 = i * U;
+  const uint32_t* src = F.words + w0;
+  if (w0 + U <= F.nwords) {
+    if constexpr (U == 2) {
+      const uint2 v = ldg_v2(src);
+      r.u[0] = v.x;
+      r.u[1] = v.y;
+    } else {
+#pragma unroll
+      for (int h = 0; h < U / 4; ++h) {
+        const uint4 v = ldg_v4(src + 4 * h);
+        r.u[4 * h + 0] = v.x;
+        r.u[4 * h + 1] = v.y;
+        r.u[4 * h + 2] = v.z;
+        r.u[4 * h + 3] = v.w;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < U; ++k) r.u[k] = (w0 + k < F.nwords) ? __ldg(src + k) : 0u;
+  }
+  r.u[U] = (w0 + U < F.nwords) ? __ldg(src + U) : 0u;
+}
+
+// Writes fetched units into a shared-memory column with stride `stride`.
+template <int S>
+__device__ __forceinline__ void put_units(uint32_t* col, const UnitRegs<S>& r, int stride) {
+#pragma unroll
+  for (int k = 0; k <= S / 32; ++k) col[k * stride] = r.u[k];
 }
 
 }  // namespace dev

@@ -25,6 +25,7 @@ struct LaunchShape {
   uint32_t cmax;     // scratch symbols per subsequence
   uint32_t long_cap; // symbols of long codes kept in shared memory
   uint32_t grid;     // persistent blocks (0: full occupancy)
+  uint32_t lut16;    // 1: the decode-and-write kernel uses 16-bit first-level entries
 };
 
 // Dynamic shared memory of the single-pass gap-array kernel.
@@ -36,6 +37,9 @@ cudaError_t launch_decode_two_phase(const DecodeParams& p, const LaunchShape& s,
 
 // Dynamic shared memory of the decode-and-write kernel (s.window = window).
 size_t two_phase_smem_bytes(const LaunchShape& s);
+
+// Dynamic shared memory of the count kernel.
+size_t count_smem_bytes(const LaunchShape& s);
 
 // Bytes per stored codeword count for subsequences of S bits.
 size_t count_bytes_per_subsequence(uint32_t S);

@@ -33,8 +33,6 @@ namespace {
 
 using namespace dev;
 
-constexpr int kSegTiles = 256;
-
 template <int S>
 struct CountT {
   using T = uint8_t;
@@ -55,7 +53,7 @@ __device__ __forceinline__ uint32_t walk(const Tables& T, const uint32_t* col, u
                                          uint32_t end, uint32_t& c) {
   bool bad = false;
   while (p < end) {
-    p += code_len(T, peek<STRIDE>(col, p), bad);
+    p += code_len8(T, peek<STRIDE>(col, p), bad);
     ++c;
   }
   return p;
@@ -75,10 +73,10 @@ __device__ __forceinline__ void repath(const Tables& T, const uint32_t* col, uin
     }
     if (a >= end && b >= end) break;
     if (a < b) {
-      a += code_len(T, peek<STRIDE>(col, a), bad);
+      a += code_len8(T, peek<STRIDE>(col, a), bad);
       ++ca;
     } else {
-      b += code_len(T, peek<STRIDE>(col, b), bad);
+      b += code_len8(T, peek<STRIDE>(col, b), bad);
       ++cb;
     }
   }
@@ -167,8 +165,7 @@ template <int S, int B>
 __device__ __forceinline__ uint32_t sync_tile(const DecodeParams& P, const FieldDesc& F,
                                               const Tables& T, bool table_ok, uint64_t g,
                                               bool guess, uint32_t a0, uint32_t* s_bits,
-                                              uint32_t* s_pre, const SyncShared& sh,
-                                              bool fix) {
+                                              uint32_t* s_pre, const SyncShared& sh) {
   using CT = typename CountT<S>::T;
   constexpr int PRE = presync_lanes<S>();
   const int t = threadIdx.x, warp = t >> 5;
@@ -202,10 +199,7 @@ __device__ __forceinline__ uint32_t sync_tile(const DecodeParams& P, const Field
   const bool overran = __syncthreads_or(flags & 1u) != 0;
   const uint32_t C = block_sum<B>(c, sh.s_warp);
   if (t == 0) {
-    const uint32_t oldC = fix ? P.tile_total[g] : 0u;
     P.tile_total[g] = C;
-    atomicAdd(reinterpret_cast<unsigned long long*>(P.seg_total + g / kSegTiles),
-              static_cast<unsigned long long>(C) - static_cast<unsigned long long>(oldC));
     P.tile_a[g] = static_cast<uint8_t>(a0);
     P.tile_e[g + 1] = static_cast<uint8_t>(sh.s_x[1]);
     P.tile_flag[g] = overran ? 1u : 0u;
@@ -219,10 +213,9 @@ __global__ void __launch_bounds__(B) k_sync(const __grid_constant__ DecodeParams
   constexpr int W = S / 32 + 1;
   constexpr int PRE = presync_lanes<S>();
   extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* s_lut = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* s_bits = s_lut + (1u << P.K);
+  uint8_t* s_lut = smem;  // length table
+  uint32_t* s_bits = reinterpret_cast<uint32_t*>(smem + lut_bytes(Lut::k8, P.K));
   uint32_t* s_pre = s_bits + W * B;
-  uint16_t* s_long = reinterpret_cast<uint16_t*>(s_pre + W * PRE);
   __shared__ uint64_t s_end[34];
   __shared__ uint32_t s_base[34];
   __shared__ uint32_t s_meta[3];
@@ -238,21 +231,12 @@ __global__ void __launch_bounds__(B) k_sync(const __grid_constant__ DecodeParams
     const FieldDesc& F = field_of(P, LS, fi);
     if (fi != cur_field) {
       __syncthreads();
-      load_table(F.table, P.K, s_lut, s_end, s_base, s_meta, B, s_long, P.long_cap);
+      load_table(F.table, P.K, F.alphabet, Lut::k8, s_lut, s_end, s_base, s_meta, B);
       cur_field = fi;
       __syncthreads();
     }
-    const Tables T{s_lut,
-                   s_end,
-                   s_base,
-                   reinterpret_cast<const uint16_t*>(reinterpret_cast<const char*>(F.table) +
-                                                     kTableHeaderBytes + (4u << P.K)),
-                   s_long,
-                   s_meta[2],
-                   P.long_cap,
-                   s_meta[0],
-                   32u - P.K};
-    sync_tile<S, B>(P, F, T, s_meta[1] == 0, g, true, 0u, s_bits, s_pre, sh, false);
+    const Tables T = make_tables(F, P.K, s_lut, s_end, s_base, s_meta, nullptr, 0);
+    sync_tile<S, B>(P, F, T, s_meta[1] == 0, g, true, 0u, s_bits, s_pre, sh);
   }
 }
 
@@ -300,10 +284,9 @@ __global__ void __launch_bounds__(B) k_fix(const __grid_constant__ DecodeParams 
   constexpr int W = S / 32 + 1;
   constexpr int PRE = presync_lanes<S>();
   extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* s_lut = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* s_bits = s_lut + (1u << P.K);
+  uint8_t* s_lut = smem;  // length table
+  uint32_t* s_bits = reinterpret_cast<uint32_t*>(smem + lut_bytes(Lut::k8, P.K));
   uint32_t* s_pre = s_bits + W * B;
-  uint16_t* s_long = reinterpret_cast<uint16_t*>(s_pre + W * PRE);
   __shared__ uint64_t s_end[34];
   __shared__ uint32_t s_base[34];
   __shared__ uint32_t s_meta[3];
@@ -318,25 +301,16 @@ __global__ void __launch_bounds__(B) k_fix(const __grid_constant__ DecodeParams 
     const FieldDesc& F = field_of(P, LS, fi);
     if (F.nunits == 0) continue;
     __syncthreads();  // the previous field's table is no longer read
-    load_table(F.table, P.K, s_lut, s_end, s_base, s_meta, B, s_long, P.long_cap);
+    load_table(F.table, P.K, F.alphabet, Lut::k8, s_lut, s_end, s_base, s_meta, B);
     __syncthreads();
-    const Tables T{s_lut,
-                   s_end,
-                   s_base,
-                   reinterpret_cast<const uint16_t*>(reinterpret_cast<const char*>(F.table) +
-                                                     kTableHeaderBytes + (4u << P.K)),
-                   s_long,
-                   s_meta[2],
-                   P.long_cap,
-                   s_meta[0],
-                   32u - P.K};
+    const Tables T = make_tables(F, P.K, s_lut, s_end, s_base, s_meta, nullptr, 0);
     const bool table_ok = s_meta[1] == 0;
     const uint64_t g0 = F.unit_begin, g1 = F.unit_begin + F.nunits;
     uint64_t cursor = g0 + 1;
     while (table_ok && cursor < g1) {
       const uint64_t gb = first_broken<B>(P, cursor, g1, &s_first);
       if (gb >= g1) break;
-      sync_tile<S, B>(P, F, T, table_ok, gb, false, P.tile_e[gb], s_bits, s_pre, sh, true);
+      sync_tile<S, B>(P, F, T, table_ok, gb, false, P.tile_e[gb], s_bits, s_pre, sh);
       cursor = gb + 1;
     }
     if (threadIdx.x == 0) {
@@ -390,8 +364,7 @@ cudaError_t launch_s(const DecodeParams& p, const LaunchShape& s, int num_sms,
 size_t sync_smem_bytes(const LaunchShape& s) {
   const size_t W = s.S / 32 + 1;
   const size_t pre = 1024 / s.S < 32 ? 1024 / s.S : 32;
-  size_t b = (static_cast<size_t>(1) << s.K) * 4 + W * s.threads * 4 + W * pre * 4;
-  b += static_cast<size_t>(s.long_cap) * 2;
+  const size_t b = dev::lut_bytes(dev::Lut::k8, s.K) + W * s.threads * 4 + W * pre * 4;
   return (b + 15) & ~static_cast<size_t>(15);
 }
 

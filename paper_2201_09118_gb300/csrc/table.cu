@@ -34,8 +34,12 @@ __device__ void build_table(const FieldDesc& F, uint32_t K) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const uint32_t A = F.alphabet;
   TableHeader* H = const_cast<TableHeader*>(F.table);
-  uint32_t* lut = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(H) + kTableHeaderBytes);
-  uint16_t* sorted = reinterpret_cast<uint16_t*>(lut + (1u << K));
+  char* tb = reinterpret_cast<char*>(H);
+  uint32_t* lut = reinterpret_cast<uint32_t*>(tb + kTableHeaderBytes);
+  uint16_t* sorted = reinterpret_cast<uint16_t*>(tb + table_sorted_off(K));
+  uint16_t* lut16 = reinterpret_cast<uint16_t*>(tb + table_lut16_off(K, A));
+  uint8_t* len8 = reinterpret_cast<uint8_t*>(tb + table_len8_off(K, A));
+  const bool with16 = lut16_usable(K, A);
 
   if (t < 34) {
     cnt[t] = 0;
@@ -126,14 +130,26 @@ __device__ void build_table(const FieldDesc& F, uint32_t K) {
     const uint32_t w = p << (32 - K);
     uint32_t L = 1;
     while (L <= 32 && static_cast<uint64_t>(w) >= s_end[L]) ++L;
-    uint32_t e;
+    uint32_t e, e16, e8;
     if (L <= K && L <= maxlen) {
       const uint32_t rank = (w >> (32 - L)) + s_base[L];
       e = (L << 16) | sorted[rank];
+      e16 = (L << 12) | (sorted[rank] & 0xFFFu);
+      e8 = L;
     } else {
-      e = kLongFlag | (L <= maxlen ? L : 33u);
+      // length of the code at the last window with this prefix
+      const uint32_t w_last = w | ((1u << (32 - K)) - 1u);
+      uint32_t Lx = L;
+      while (Lx <= 32 && static_cast<uint64_t>(w_last) >= s_end[Lx]) ++Lx;
+      const uint32_t lmin = L <= maxlen ? L : 33u;
+      const uint32_t lmax = Lx <= maxlen ? Lx : 0xFFu;
+      e = kLongFlag | (lmax << 8) | lmin;
+      e16 = lmin | (lmin == lmax ? 0u : kLut16Mixed);
+      e8 = lmin == lmax ? lmin : (kLen8Walk | lmin);
     }
     lut[p] = e;
+    if (with16) lut16[p] = static_cast<uint16_t>(e16);
+    len8[p] = static_cast<uint8_t>(e8);
   }
 }
 
@@ -167,7 +183,7 @@ cudaError_t launch_prepare(const PrepParams& p, cudaStream_t stream) {
 }
 
 size_t table_bytes(uint32_t K, uint32_t alphabet) {
-  size_t b = kTableHeaderBytes + (static_cast<size_t>(1) << K) * 4 + static_cast<size_t>(alphabet) * 2;
+  const size_t b = table_len8_off(K, alphabet) + (static_cast<size_t>(1) << K);
   return (b + 255) & ~static_cast<size_t>(255);
 }
 
