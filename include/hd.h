@@ -116,11 +116,15 @@ typedef struct hd_config {
   uint32_t subseq_bits; /* decoder subsequence bits.  Gap-array decode: a multiple
                            of the field's S, <= 512 (0 = max(256, S));
                            self-synchronisation: 64, 128 or 256 (512 acts as
-                           256; 0 = the field's S) */
+                           256; 0 = 256); hd_sync_points always uses the
+                           field's S */
   uint32_t threads;     /* threads per block = subsequences per tile: 128, 256, 512 */
   uint32_t window;      /* shared-memory output window in symbols (Alg. 1 buffer);
                            0 = sized from the field's mean code length */
-  uint32_t lut_bits;    /* first-level decode-table index bits, 8 .. 13 */
+  uint32_t lut_bits;    /* first-level decode-table index bits, 8 .. 15 (0 = 13
+                           for alphabets up to 4096, whose tables have 16-bit
+                           entries, else 12); a shape whose tables do not fit
+                           shared memory fails with HD_ERR_ARG */
 } hd_config;
 
 /* Sets the launch shape used by later decodes on this context (NULL resets to
@@ -171,7 +175,7 @@ int hd_batch_status(hd_ctx* ctx, int32_t* status, uint32_t nf, void* stream);
  * every candidate shape -- decoder subsequence bits {64, 128, 256, 512} (a
  * multiple of the largest stream S for gap arrays, at most 256 for
  * self-synchronisation) x threads {128, 256, 512} x first-level table bits
- * {11, 12, 13}, window sized from the mean code length -- timing three
+ * {11, 12, 13, 14}, window sized from the mean code length -- timing three
  * replays of each with CUDA events, and keeps the fastest shape that decodes
  * every field without error.  The choice is stored in the context per batch
  * class (strategy, mean code length in quarter bits, log2 of the symbol

@@ -63,6 +63,9 @@ namespace {
 using hd::FieldDesc;
 
 constexpr uint32_t kDefaultThreads = 256;
+// first-level table bits when the configuration leaves them open: 13 with
+// 16-bit entries (alphabets up to 4096), else 12
+constexpr uint32_t kDefaultK16 = 13;
 constexpr uint32_t kDefaultK = 12;
 
 struct DeviceGuard {
@@ -144,12 +147,12 @@ int check_field(const hd_field* f, bool need_out, const void* out) {
   return HD_OK;
 }
 
-// Decoder subsequence when the configuration leaves it open: gap-array
-// decodes take 256-bit subsequences (every second gap entry of a 128-bit
-// stream) because the per-tile work of a thread then amortises its fixed
-// costs better; the synchronising kernel uses the stream's own size.
+// Decoder subsequence when the configuration leaves it open: 256 bits (for
+// gap arrays every second entry of a 128-bit stream's array), because the
+// per-tile work of a thread then amortises its fixed costs better and, when
+// synchronising, fewer boundaries have to be agreed on.
 uint32_t default_decoder_S(uint32_t stream_S, bool gap) {
-  if (!gap) return stream_S;
+  if (!gap) return 256;
   return stream_S < 256 ? 256 : stream_S;
 }
 
@@ -157,7 +160,7 @@ hd::LaunchShape shape_for(const hd_ctx* c, uint32_t stream_S, bool gap) {
   hd::LaunchShape s{};
   s.S = c->cfg.subseq_bits ? c->cfg.subseq_bits : default_decoder_S(stream_S, gap);
   s.threads = c->cfg.threads ? c->cfg.threads : kDefaultThreads;
-  s.K = c->cfg.lut_bits ? c->cfg.lut_bits : kDefaultK;
+  s.K = c->cfg.lut_bits;  // 0: chosen per launch
   s.window = c->cfg.window;  // 0: chosen per launch
   s.grid = 0;
   return s;
@@ -255,6 +258,7 @@ int prepare_launch(const hd_ctx* c, std::vector<FieldDesc>& descs, const hd::Lau
   const double bits_per = static_cast<double>(bits) / static_cast<double>(syms ? syms : 1);
   // symbols of codes longer than the first-level table, kept in shared memory
   s.long_cap = static_cast<uint32_t>(align_up(std::min<uint32_t>(amax, 4096), 8));
+  if (s.K == 0) s.K = hd::lut16_usable(kDefaultK16, amax) ? kDefaultK16 : kDefaultK;
   // 16-bit first-level entries when every field's symbols fit 12 bits
   s.lut16 = hd::lut16_usable(s.K, amax) ? 1u : 0u;
   if (s.window == 0) {
@@ -555,7 +559,7 @@ hd::LaunchShape group_shape(const hd_ctx* c, const hd_field* fs, const std::vect
   s.S = use.subseq_bits ? use.subseq_bits : default_decoder_S(maxS ? maxS : 128, gap);
   if (!gap && s.S > 256) s.S = 256;
   s.threads = use.threads ? use.threads : kDefaultThreads;
-  s.K = use.lut_bits ? use.lut_bits : kDefaultK;
+  s.K = use.lut_bits;  // 0: chosen per launch
   s.window = use.window;
   return s;
 }
@@ -703,7 +707,7 @@ int hd_set_config(hd_ctx* c, const hd_config* cfg) {
   if (cfg->subseq_bits && !valid_S(cfg->subseq_bits) && cfg->subseq_bits != 512) return HD_ERR_ARG;
   if (cfg->threads && cfg->threads != 128 && cfg->threads != 256 && cfg->threads != 512)
     return HD_ERR_ARG;
-  if (cfg->lut_bits && (cfg->lut_bits < 8 || cfg->lut_bits > 13)) return HD_ERR_ARG;
+  if (cfg->lut_bits && (cfg->lut_bits < 8 || cfg->lut_bits > 15)) return HD_ERR_ARG;
   if (cfg->window && (cfg->window < 64 || cfg->window > 32768)) return HD_ERR_ARG;
   c->cfg = *cfg;
   return HD_OK;
@@ -715,7 +719,7 @@ int hd_get_config(hd_ctx* c, hd_config* cfg) {
   cfg->subseq_bits = c->cfg.subseq_bits;
   cfg->threads = c->cfg.threads ? c->cfg.threads : kDefaultThreads;
   cfg->window = c->cfg.window ? c->cfg.window : c->last_shape.window;
-  cfg->lut_bits = c->cfg.lut_bits ? c->cfg.lut_bits : kDefaultK;
+  cfg->lut_bits = c->cfg.lut_bits ? c->cfg.lut_bits : c->last_shape.K;
   return HD_OK;
 }
 
@@ -739,6 +743,7 @@ static int decode_impl(hd_ctx* c, const hd_field* f, uint16_t* d_out, uint8_t* g
   const bool self_sync = sync_only || f->gap == nullptr;
   hd::LaunchShape s = shape_for(c, f->subseq_bits, !self_sync);
   if (self_sync && s.S > 256) s.S = 256;  // the synchronising kernel stops at 256-bit subsequences
+  if (sync_only) s.S = f->subseq_bits;    // one gap entry per stream subsequence
   if (!self_sync && (s.S % f->subseq_bits)) {
     c->host_status = HD_ERR_ARG;
     return HD_ERR_ARG;
@@ -822,7 +827,7 @@ int hd_autotune(hd_ctx* c, const hd_field* fs, uint32_t nf, uint16_t* const* d_o
     }
     const uint32_t S_list[4] = {64, 128, 256, 512};
     const uint32_t B_list[3] = {128, 256, 512};
-    const uint32_t K_list[3] = {11, 12, 13};
+    const uint32_t K_list[4] = {11, 12, 13, 14};
     double best_ms = 1e30;
     hd_config best_cfg{};
     for (uint32_t S : S_list) {

@@ -95,7 +95,7 @@ def test_launch_shapes(ctx, S, threads, with_gap):
     x = synth.laplace_codes(200003, scale=30.0, seed=S + threads)
     c = oracle.compress(x, 1024, S=S)
     try:
-        for window, K in ((S, 8), (1024, 11), (0, 12), (8192, 13)):
+        for window, K in ((S, 8), (1024, 11), (0, 12), (8192, 13), (0, 14), (2048, 15)):
             ctx.set_config(subseq_bits=S, threads=threads, window=max(window, S) if window else 0,
                            lut_bits=K)
             check(ctx, c, with_gap)
