@@ -128,7 +128,9 @@ typedef struct hd_config {
 } hd_config;
 
 /* Sets the launch shape used by later decodes on this context (NULL resets to
- * defaults).  HD_ERR_ARG for values outside the ranges above. */
+ * defaults).  HD_ERR_ARG for values outside the ranges above.  hd_get_config
+ * reports the configured values, with the shape of the last decode in place
+ * of those left at 0. */
 int hd_set_config(hd_ctx* ctx, const hd_config* cfg);
 int hd_get_config(hd_ctx* ctx, hd_config* cfg);
 
@@ -180,7 +182,8 @@ int hd_batch_status(hd_ctx* ctx, int32_t* status, uint32_t nf, void* stream);
  * every field without error.  The choice is stored in the context per batch
  * class (strategy, mean code length in quarter bits, log2 of the symbol
  * count, largest stream S) and used by later hd_decode_batch calls of that
- * class while the context's configuration is all zero.  `best` (may be NULL)
+ * class, and by hd_decode / hd_decode_host calls of a single field of that
+ * class, while the context's configuration is all zero.  `best` (may be NULL)
  * receives the shape chosen for the first strategy group.  Synchronous; the
  * outputs hold the batch's symbols afterwards.  HD_ERR_CORRUPT if no
  * candidate decodes the batch cleanly. */

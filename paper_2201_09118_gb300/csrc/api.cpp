@@ -564,6 +564,12 @@ hd::LaunchShape group_shape(const hd_ctx* c, const hd_field* fs, const std::vect
   return s;
 }
 
+// Launch shape of a single-field decode: as for a batch of that one field.
+hd::LaunchShape field_shape(const hd_ctx* c, const hd_field* f, bool gap) {
+  const std::vector<uint32_t> one{0};
+  return group_shape(c, f, one, gap);
+}
+
 struct BatchPlan {
   std::vector<uint32_t> gap_i, sync_i;  // fields with work, by strategy
 };
@@ -716,8 +722,9 @@ int hd_set_config(hd_ctx* c, const hd_config* cfg) {
 int hd_get_config(hd_ctx* c, hd_config* cfg) {
   if (!c || !cfg) return HD_ERR_ARG;
   std::lock_guard<std::mutex> lk(c->mu);
-  cfg->subseq_bits = c->cfg.subseq_bits;
-  cfg->threads = c->cfg.threads ? c->cfg.threads : kDefaultThreads;
+  cfg->subseq_bits = c->cfg.subseq_bits ? c->cfg.subseq_bits : c->last_shape.S;
+  cfg->threads = c->cfg.threads ? c->cfg.threads
+                 : c->last_shape.threads ? c->last_shape.threads : kDefaultThreads;
   cfg->window = c->cfg.window ? c->cfg.window : c->last_shape.window;
   cfg->lut_bits = c->cfg.lut_bits ? c->cfg.lut_bits : c->last_shape.K;
   return HD_OK;
@@ -741,7 +748,8 @@ static int decode_impl(hd_ctx* c, const hd_field* f, uint16_t* d_out, uint8_t* g
     return HD_OK;
   }
   const bool self_sync = sync_only || f->gap == nullptr;
-  hd::LaunchShape s = shape_for(c, f->subseq_bits, !self_sync);
+  hd::LaunchShape s = sync_only ? shape_for(c, f->subseq_bits, false)
+                                : field_shape(c, f, !self_sync);
   if (self_sync && s.S > 256) s.S = 256;  // the synchronising kernel stops at 256-bit subsequences
   if (sync_only) s.S = f->subseq_bits;    // one gap entry per stream subsequence
   if (!self_sync && (s.S % f->subseq_bits)) {

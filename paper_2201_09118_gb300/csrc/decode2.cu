@@ -270,10 +270,18 @@ __global__ void __launch_bounds__(B, write_min_blocks<B>())
                     [&](uint16_t* dst) {
                       uint32_t p = gp;
                       bool bad = false;
-                      for (uint32_t j = 0; j < c; ++j) {
-                        uint32_t sym;
-                        p += code_sym_t<E>(T, peek<B>(col, p), sym, bad);
-                        dst[j] = static_cast<uint16_t>(sym);
+                      uint32_t j = 0;
+                      for (; j + 1 < c; j += 2) {
+                        uint32_t s0, s1;
+                        p += code_sym_t<E>(T, peek<B>(col, p), s0, bad);
+                        p += code_sym_t<E>(T, peek<B>(col, p), s1, bad);
+                        dst[j] = static_cast<uint16_t>(s0);
+                        dst[j + 1] = static_cast<uint16_t>(s1);
+                      }
+                      if (j < c) {
+                        uint32_t s0;
+                        p += code_sym_t<E>(T, peek<B>(col, p), s0, bad);
+                        dst[j] = static_cast<uint16_t>(s0);
                       }
                       if (bad) atomicOr(F.err, kErrCode);
                     });

@@ -202,7 +202,9 @@ __device__ __forceinline__ bool backoff_wait(const DecodeParams& P, uint64_t t0)
 // shared-memory window of `window` symbols.  A thread decodes its whole range
 // [o, o + c) into the window only when it fits; the first thread that does
 // not fit ends the window, the window is written to global memory with
-// coalesced 16-byte stores, and the next window starts at that thread.
+// coalesced 16-byte stores, and the next window starts at that thread.  When
+// the whole tile fits (the usual case, the window being sized for it) one
+// pass with two barriers does it.
 // `decode(dst)` writes the thread's c symbols to dst[0 .. c).
 // Requires window >= max c (c <= S).  Global writes are clipped to [0, n).
 template <int B, class DecodeFn>
@@ -214,6 +216,31 @@ __device__ __forceinline__ void window_write(uint16_t* s_out, uint32_t* s_flush_
   const uint32_t off0 = static_cast<uint32_t>((reinterpret_cast<uintptr_t>(out) >> 1) & 7u);
   // out - off0 is 16-byte aligned; virtual index X = x + off0
   uint16_t* out_al = out - off0;
+  if (C <= window) {
+    const uint64_t X0 = base + off0;
+    const uint32_t pad = static_cast<uint32_t>(X0 & 7u);
+    if (c) decode(s_out + pad + o);
+    __syncthreads();
+    const uint64_t a0 = X0 - pad;
+    uint16_t* dst = out_al + a0;
+    const uint32_t end_r = pad + C;
+    const uint64_t Xn = n + off0;  // first virtual index past the output
+    const uint32_t end_ok =
+        a0 >= Xn ? 0u : (Xn - a0 < end_r ? static_cast<uint32_t>(Xn - a0) : end_r);
+    const uint32_t nvec = (end_r + 7) >> 3;
+    for (uint32_t v = t; v < nvec; v += B) {
+      const uint32_t r0 = v << 3;
+      if (r0 >= pad && r0 + 8 <= end_ok) {
+        *reinterpret_cast<uint4*>(dst + r0) = *reinterpret_cast<const uint4*>(s_out + r0);
+      } else {
+        const uint32_t lo = r0 > pad ? r0 : pad;
+        const uint32_t hi = r0 + 8 < end_ok ? r0 + 8 : end_ok;
+        for (uint32_t r = lo; r < hi; ++r) dst[r] = s_out[r];
+      }
+    }
+    __syncthreads();
+    return;
+  }
   bool done = c == 0;
   uint32_t ws = 0;
   while (ws < C) {
