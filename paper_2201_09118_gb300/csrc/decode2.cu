@@ -165,45 +165,60 @@ __global__ void __launch_bounds__(B, count_min_blocks<B>())
 }
 
 // One block of kScanThreads: tile_base[g] = sum of tile_total[j] for j < g,
-// over all tiles of the launch (g in [0, units]).  Each thread owns a
-// contiguous run of tiles.
+// over all tiles of the launch (g in [0, units]).  The tiles are taken in
+// passes of kScanThreads * kScanPer; in a pass each thread owns kScanPer
+// consecutive tiles, whose totals it loads at once (independent loads), and a
+// block scan of the per-thread sums gives each run's first base.
 constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 16;
 
 __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ DecodeParams P) {
   __shared__ uint64_t s_part[kScanThreads / 32];
+  __shared__ uint64_t s_carry;
   const LaunchSize LS = launch_size(P);
   const uint64_t n = LS.units;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const uint64_t per = (n + kScanThreads - 1) / kScanThreads;
-  const uint64_t a = per * t < n ? per * t : n;
-  const uint64_t b = a + per < n ? a + per : n;
-  uint64_t sum = 0;
-  for (uint64_t j = a; j < b; ++j) sum += P.tile_total[j];
-  // exclusive block scan of the per-thread sums
-  uint64_t incl = sum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += u;
-  }
-  if (lane == 31) s_part[warp] = incl;
+  if (t == 0) s_carry = 0;
   __syncthreads();
-  if (warp == 0) {
-    uint64_t v = s_part[lane];
+  for (uint64_t p0 = 0; p0 < n; p0 += static_cast<uint64_t>(kScanThreads) * kScanPer) {
+    const uint64_t a = p0 + static_cast<uint64_t>(t) * kScanPer;
+    uint32_t v[kScanPer];
+    uint64_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      v[k] = a + k < n ? P.tile_total[a + k] : 0u;
+      sum += v[k];
+    }
+    uint64_t incl = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint64_t u = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += u;
+      const uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
     }
-    s_part[lane] = v;
+    if (lane == 31) s_part[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      uint64_t x = s_part[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t u = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += u;
+      }
+      s_part[lane] = x;
+    }
+    __syncthreads();
+    uint64_t run = s_carry + (warp ? s_part[warp - 1] : 0ull) + incl - sum;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      if (a + k < n) P.tile_base[a + k] = run;
+      run += v[k];
+    }
+    const uint64_t pass_total = s_part[kScanThreads / 32 - 1];
+    __syncthreads();
+    if (t == 0) s_carry += pass_total;
+    __syncthreads();
   }
-  __syncthreads();
-  uint64_t run = (warp ? s_part[warp - 1] : 0ull) + incl - sum;
-  for (uint64_t j = a; j < b; ++j) {
-    P.tile_base[j] = run;
-    run += P.tile_total[j];
-  }
-  if (t == kScanThreads - 1) P.tile_base[n] = s_part[kScanThreads / 32 - 1];
+  if (t == 0) P.tile_base[n] = s_carry;
 }
 
 template <int S, int B, class E>
