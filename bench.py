@@ -46,6 +46,33 @@ def _env_int(k, d):
         return d
 
 
+def ranks_max(vals, dist, device):
+    """Element-wise maximum over ranks (the slowest rank's times); identity
+    without a process group."""
+    if not dist:
+        return [float(v) for v in vals]
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def ranks_min(vals, dist, device):
+    """Element-wise minimum over ranks."""
+    if not dist:
+        return [float(v) for v in vals]
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MIN)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_gbps(codes_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Decoded GB/s of the whole job: every rank's uint16 output over the
+    slowest rank's time (ranks decode equal-sized replicas)."""
+    return 2.0 * codes_per_rank * steps * world / (max_ms * 1e-3) / 1e9
+
+
 def workload_codes(side: int, seed: int):
     import synth
     return synth.field3d_codes(side, rel_eb=1e-4, noise=0.01, seed=seed)
@@ -445,10 +472,7 @@ def run_gpu(args):
     ms_ss, kms_ss, kl_ss, _, st_ss = timed(field_ss, max(3, args.steps // 2), 2)
     launch_ss = ctx.get_config()
 
-    if dist:
-        t = torch.tensor([ms, ms_ss], dtype=torch.float64, device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_ss = float(t[0]), float(t[1])
+    ms, ms_ss = ranks_max([ms, ms_ss], dist, f"cuda:{dev}")
 
     # end to end through the host-buffer entry point (pinned host memory)
     words_h = torch.from_numpy(enc["words"].view(np.int32)).pin_memory()
@@ -470,11 +494,8 @@ def run_gpu(args):
         if k >= 2:
             e2e_times.append(t1 - t0)
     assert np.array_equal(out_h.numpy().view(np.uint16), codes)
-    e2e_gbps = 2.0 * n / statistics.median(e2e_times) / 1e9
-    if dist:
-        t = torch.tensor([e2e_gbps], dtype=torch.float64, device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MIN)
-        e2e_gbps = float(t[0]) * world
+    e2e_gbps = ranks_min([2.0 * n / statistics.median(e2e_times) / 1e9], dist,
+                         f"cuda:{dev}")[0] * world
 
     if rank != 0:
         if dist:
@@ -492,7 +513,7 @@ def run_gpu(args):
     kernel_ms = kms / max(1, kl)
     achieved = nbytes_alg / (kernel_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
-    value = 2.0 * n * args.steps * world / (ms * 1e-3) / 1e9
+    value = whole_job_gbps(n, args.steps, world, ms)
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -511,7 +532,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": int(2 * n)},
         "clocks": clocks,
         "gpu_launches": int(launches),
-        "selfsync": {"value": 2.0 * n * max(3, args.steps // 2) * world / (ms_ss * 1e-3) / 1e9,
+        "selfsync": {"value": whole_job_gbps(n, max(3, args.steps // 2), world, ms_ss),
                      "unit": "GB/s", "kernel_ms": kms_ss / max(1, kl_ss), "status": st_ss,
                      "launch": launch_ss},
     }

@@ -304,6 +304,26 @@ def test_full_512cube(ctx, cube, with_gap):
     assert np.all(res[c["n"]:] == np.uint16(CANARY))
 
 
+@pytest.mark.parametrize("with_gap", [True, False], ids=["gap", "selfsync"])
+def test_full_512cube_in_the_benchmark_launch_shape(cube, with_gap):
+    # the benchmark times the shape the autotuner picks for this field
+    from paper_2201_09118_gb300 import hd
+    x, c = cube
+    tctx = hd.Context(0)
+    f = dev_field(c, with_gap)
+    out = torch.full((c["n"] + 64,), CANARY, dtype=torch.int32).to(torch.int16).cuda()
+    best = tctx.autotune([f], [out])
+    assert best["threads"] in (128, 256, 512)
+    out.fill_(CANARY - 65536)
+    tctx.decode(f, out)
+    assert tctx.status() == 0
+    assert tctx.get_config()["threads"] == best["threads"]
+    res = out.cpu().numpy().view(np.uint16)
+    assert np.array_equal(res[:c["n"]], x)
+    assert np.all(res[c["n"]:] == np.uint16(CANARY))
+    tctx.close()
+
+
 def test_full_512cube_matches_oracle_decode(ctx, cube):
     x, c = cube
     assert np.array_equal(expect(c), x)
