@@ -103,15 +103,18 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, n_codes: int):
+def recorded_traffic(kernel: str, n_codes: int, launch: dict):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+    the current kernel source in the same launch shape (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
         e = d[kernel]
         if e.get("source_hash") != kernel_source_hash():
+            return None
+        shape = e.get("shape", {})
+        if any(launch.get(k) != v for k, v in shape.items()):
             return None
         return float(e["dram_bytes_per_launch"]) * n_codes / float(e["n_codes"])
     except Exception:
@@ -524,7 +527,7 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}", "launch": launch_gap,
                    "autotuned": tuned},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": recorded_traffic("decode_gap", n),
+                     "frac": achieved / peak, "traffic": recorded_traffic("decode_gap", n, launch_gap),
                      "peak_kind": peak_kind, "kernel": "k_count + k_write",
                      "kernel_ms": kernel_ms, "algorithmic_bytes": nbytes_alg},
         "e2e": {"value": e2e_gbps, "unit": "GB/s",
