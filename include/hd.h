@@ -196,8 +196,14 @@ int hd_graph_stats(hd_ctx* ctx, uint64_t* captures, uint32_t* cached);
 
 /* Host-buffer decode: `f` holds HOST pointers (pinned memory is fastest),
  * host_out receives f->n symbols.  Copies the stream, gap array and lengths
- * to context-owned device buffers, decodes and copies the symbols back, all
- * on `stream`; returns when done with the decode status. */
+ * to context-owned device buffers, decodes and copies the symbols back;
+ * returns when done with the decode status.  Large gap-array fields run as a
+ * pipeline (the transfers belong to the paper's end-to-end comparison,
+ * Sec. V): the stream goes to the device in chunks of whole tiles on one copy
+ * stream, each chunk is counted, scanned and decoded on `stream` once its bits
+ * have arrived, and its symbols return on a second copy stream once written,
+ * so both transfer directions and the kernels overlap.  Other fields are
+ * copied, decoded and copied back in sequence on `stream`. */
 int hd_decode_host(hd_ctx* ctx, const hd_field* f, uint16_t* host_out, void* stream);
 
 /* Allocation-free gap-array decode.  Some callers cannot call cudaMalloc

@@ -54,6 +54,11 @@ struct hd_ctx {
   cudaEvent_t pinned_ev = nullptr;
   bool pinned_busy = false;
   cudaEvent_t tune_ev[2] = {nullptr, nullptr};  // autotuner timing
+  // pipelined host decode: copy streams, per-chunk events, pinned chunk ends
+  cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+  std::vector<cudaEvent_t> pipe_ev;
+  uint64_t* pin_ends = nullptr;      // host-mapped: chunk ends written by the tile scan
+  uint64_t* pin_ends_dev = nullptr;  // the same memory as the device sees it
   // autotuner results: batch class -> launch shape
   std::map<TuneKey, hd_config> tuned;
 };
@@ -651,6 +656,147 @@ int decode_batch_locked(hd_ctx* c, const hd_field* fs, uint32_t nf, uint16_t* co
   return HD_OK;
 }
 
+
+constexpr uint32_t kMaxChunks = 16;
+
+// hd_decode_host for a large gap-array field as a copy/decode pipeline (the
+// host-to-device transfer is part of the paper's end-to-end comparison,
+// Sec. V): the stream is copied to the device in chunks of whole tiles on one
+// copy stream, each chunk is counted, scanned and decoded on the caller's
+// stream as soon as its bits have arrived, and its symbols go back to the host
+// on a second copy stream as soon as they are written.  The host learns where
+// a chunk's symbols end from its tile scan (one 8-byte read per chunk), so the
+// three directions overlap.  Context lock held; `f` holds host pointers.
+int decode_host_pipelined(hd_ctx* c, const hd_field* f, uint16_t* host_out, cudaStream_t st,
+                          bool* used) {
+  *used = false;
+  const uint64_t nsub_stream = (f->nbits + f->subseq_bits - 1) / f->subseq_bits;
+  const size_t words_b = align_up(f->nwords * 4, 256);
+  const size_t gap_b = align_up(nsub_stream, 256);
+  const size_t len_b = align_up(f->alphabet, 256);
+  const size_t out_b = align_up(f->n * 2, 256);
+  hd_field d = *f;  // device copy of the field, pointers into the staging area
+  hd::LaunchShape shape = field_shape(c, &d, true);
+  if (shape.S % f->subseq_bits) return HD_OK;  // not pipelined
+  std::vector<FieldDesc> descs(1);
+  {
+    int rc = ensure_stage(c, words_b + gap_b + len_b + out_b);
+    if (rc) return rc;
+  }
+  char* p = c->stage;
+  d.words = reinterpret_cast<const uint32_t*>(p);
+  d.gap = reinterpret_cast<const uint8_t*>(p + words_b);
+  d.lengths = reinterpret_cast<const uint8_t*>(p + words_b + gap_b);
+  uint16_t* dout = reinterpret_cast<uint16_t*>(p + words_b + gap_b + len_b);
+  fill_desc(descs[0], &d, shape, dout);
+  Prepared P;
+  int rc = prepare_launch(c, descs, shape, false, P);
+  if (rc) return rc;
+  if (P.tiles < 4ull * c->num_sms) return HD_OK;  // too small to pipeline
+  const Layout L = make_layout(1, P.tiles, P.subs, P.tab_bytes, P.s, false, false);
+  rc = ensure_ws(c, L.total);
+  if (rc) return rc;
+  char* ws = c->ws;
+  bind_descs(descs, ws, L, P, false, false);
+  hd::PrepParams pp;
+  hd::DecodeParams dp;
+  make_params(descs, ws, L, P.s, false, false, 1, P.tiles, pp, dp);
+  if (!c->s_h2d && cudaStreamCreateWithFlags(&c->s_h2d, cudaStreamNonBlocking) != cudaSuccess)
+    return HD_ERR_CUDA;
+  if (!c->s_d2h && cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking) != cudaSuccess)
+    return HD_ERR_CUDA;
+  while (c->pipe_ev.size() < 3 * kMaxChunks + 1) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return HD_ERR_CUDA;
+    c->pipe_ev.push_back(e);
+  }
+  if (!c->pin_ends) {
+    void* hp = nullptr;
+    void* dptr = nullptr;
+    if (cudaHostAlloc(&hp, 8 * kMaxChunks, cudaHostAllocMapped) != cudaSuccess) {
+      cudaGetLastError();
+      return HD_ERR_NOMEM;
+    }
+    if (cudaHostGetDevicePointer(&dptr, hp, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeHost(hp);
+      return HD_ERR_CUDA;
+    }
+    c->pin_ends = static_cast<uint64_t*>(hp);
+    c->pin_ends_dev = static_cast<uint64_t*>(dptr);
+  }
+  *used = true;
+  const uint64_t units_per_sub = P.s.S / 32;
+  const uint64_t tiles = P.tiles;
+  const uint32_t nch = static_cast<uint32_t>(
+      std::min<uint64_t>(kMaxChunks, std::max<uint64_t>(1, tiles / (2ull * c->num_sms))));
+  const uint64_t per = (tiles + nch - 1) / nch;
+  cudaEvent_t* ev_in = c->pipe_ev.data();
+  cudaEvent_t* ev_end = ev_in + kMaxChunks;
+  cudaEvent_t* ev_out = ev_end + kMaxChunks;
+  cudaEvent_t ev_done = ev_out[kMaxChunks];
+  // lengths and the whole gap array (small) first, then the decode tables
+  if (cudaMemcpyAsync(p + words_b + gap_b, f->lengths, f->alphabet, cudaMemcpyHostToDevice,
+                      st) != cudaSuccess ||
+      cudaMemcpyAsync(p + words_b, f->gap, nsub_stream, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      hd::launch_prepare(pp, st) != cudaSuccess)
+    return HD_ERR_CUDA;
+  c->launches += 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->profile) {
+    e0 = next_event(c);
+    e1 = next_event(c);
+    cudaEventRecord(e0, st);
+  }
+  for (uint32_t j = 0; j < nch; ++j) {
+    const uint64_t t0 = j * per, t1 = std::min<uint64_t>(tiles, t0 + per);
+    // units of the chunk's subsequences plus the one a codeword near the end
+    // may reach
+    const uint64_t w0 = t0 * P.s.threads * units_per_sub;
+    const uint64_t w1 = std::min<uint64_t>(f->nwords, t1 * P.s.threads * units_per_sub + 1);
+    if (w1 > w0 && cudaMemcpyAsync(p + 4 * w0, f->words + w0, 4 * (w1 - w0),
+                                   cudaMemcpyHostToDevice, c->s_h2d) != cudaSuccess)
+      return HD_ERR_CUDA;
+    if (cudaEventRecord(ev_in[j], c->s_h2d) != cudaSuccess ||
+        cudaStreamWaitEvent(st, ev_in[j], 0) != cudaSuccess)
+      return HD_ERR_CUDA;
+    dp.unit_lo = t0;
+    dp.unit_hi = t1;
+    dp.scan_end = c->pin_ends_dev + j;  // the scan stores the chunk's end for the host
+    if (hd::launch_phase(dp, P.s, hd::Phase::kCount, c->num_sms, st) != cudaSuccess ||
+        hd::launch_phase(dp, P.s, hd::Phase::kScan, c->num_sms, st) != cudaSuccess ||
+        cudaEventRecord(ev_end[j], st) != cudaSuccess ||
+        hd::launch_phase(dp, P.s, hd::Phase::kWrite, c->num_sms, st) != cudaSuccess ||
+        cudaEventRecord(ev_out[j], st) != cudaSuccess)
+      return HD_ERR_CUDA;
+    c->launches += 3;
+  }
+  if (c->profile) cudaEventRecord(e1, st);
+  // symbols back to the host, chunk by chunk, as their ends become known
+  uint64_t done = 0;
+  for (uint32_t j = 0; j < nch; ++j) {
+    if (cudaEventSynchronize(ev_end[j]) != cudaSuccess) return HD_ERR_CUDA;
+    const uint64_t chunk_end = *const_cast<volatile uint64_t*>(c->pin_ends + j);
+    const uint64_t end = std::min<uint64_t>(f->n, chunk_end);
+    if (end > done) {
+      if (cudaStreamWaitEvent(c->s_d2h, ev_out[j], 0) != cudaSuccess ||
+          cudaMemcpyAsync(host_out + done, dout + done, 2 * (end - done), cudaMemcpyDeviceToHost,
+                          c->s_d2h) != cudaSuccess)
+        return HD_ERR_CUDA;
+      done = end;
+    }
+  }
+  if (cudaEventRecord(ev_done, c->s_d2h) != cudaSuccess ||
+      cudaStreamWaitEvent(st, ev_done, 0) != cudaSuccess)
+    return HD_ERR_CUDA;
+  c->err_off = L.err;
+  c->err_count = 1;
+  c->host_status = HD_OK;
+  c->last_shape = P.s;
+  return HD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -693,6 +839,10 @@ int hd_ctx_destroy(hd_ctx* c) {
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->pinned) cudaFreeHost(c->pinned);
     if (c->pinned_ev) cudaEventDestroy(c->pinned_ev);
+    if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
+    if (c->s_d2h) cudaStreamDestroy(c->s_d2h);
+    for (auto e : c->pipe_ev) cudaEventDestroy(e);
+    if (c->pin_ends) cudaFreeHost(c->pin_ends);  // cudaHostAlloc memory
     for (auto e : c->tune_ev)
       if (e) cudaEventDestroy(e);
     if (c->ws) cudaFree(c->ws);
@@ -923,6 +1073,19 @@ int hd_decode_host(hd_ctx* c, const hd_field* f, uint16_t* host_out, void* strea
   if (rc == HD_PENDING) return HD_OK;
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (f->gap && f->nbits && f->n) {
+    bool used = false;
+    rc = decode_host_pipelined(c, f, host_out, st, &used);
+    if (rc) return rc;
+    if (used) {
+      std::vector<uint32_t> bits;
+      rc = read_errors(c, stream, bits);
+      if (rc) return rc;
+      uint32_t all = 0;
+      for (uint32_t b : bits) all |= b;
+      return map_err_bits(all);
+    }
+  }
   const uint64_t nsub = (f->nbits + f->subseq_bits - 1) / f->subseq_bits;
   const size_t words_b = align_up(f->nwords * 4, 256);
   const size_t gap_b = f->gap ? align_up(nsub, 256) : 0;

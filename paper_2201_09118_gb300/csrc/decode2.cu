@@ -96,7 +96,6 @@ template <int S, int B>
 __global__ void __launch_bounds__(B, count_min_blocks<B>())
     k_count(const __grid_constant__ DecodeParams P) {
   using CT = typename CountType<S>::T;
-  constexpr int W = S / 32 + 1;
   extern __shared__ __align__(16) unsigned char smem[];
   uint8_t* s_lut = smem;  // length table
   uint32_t* s_bits = reinterpret_cast<uint32_t*>(smem + lut_bytes(Lut::k8, P.K));
@@ -109,7 +108,7 @@ __global__ void __launch_bounds__(B, count_min_blocks<B>())
   uint32_t* col = s_bits + t;
   uint32_t cur_field = 0xffffffffu;
   const LaunchSize LS = launch_size(P);
-  uint64_t g = blockIdx.x;
+  uint64_t g = LS.lo + blockIdx.x;
   TileIn<S> nxt;
   uint32_t nfi = 0;
   if (g < LS.units) {
@@ -165,7 +164,8 @@ __global__ void __launch_bounds__(B, count_min_blocks<B>())
 }
 
 // One block of kScanThreads: tile_base[g] = sum of tile_total[j] for j < g,
-// over all tiles of the launch (g in [0, units]).  The tiles are taken in
+// over the tiles of the launch (g in [unit_lo, units]; a range that starts
+// later continues from tile_base[unit_lo]).  The tiles are taken in
 // passes of kScanThreads * kScanPer; in a pass each thread owns kScanPer
 // consecutive tiles, whose totals it loads at once (independent loads), and a
 // block scan of the per-thread sums gives each run's first base.
@@ -178,9 +178,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ D
   const LaunchSize LS = launch_size(P);
   const uint64_t n = LS.units;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  if (t == 0) s_carry = 0;
+  // a range that does not start at tile 0 continues the previous range's sum
+  if (t == 0) s_carry = LS.lo ? P.tile_base[LS.lo] : 0ull;
   __syncthreads();
-  for (uint64_t p0 = 0; p0 < n; p0 += static_cast<uint64_t>(kScanThreads) * kScanPer) {
+  for (uint64_t p0 = LS.lo; p0 < n; p0 += static_cast<uint64_t>(kScanThreads) * kScanPer) {
     const uint64_t a = p0 + static_cast<uint64_t>(t) * kScanPer;
     uint32_t v[kScanPer];
     uint64_t sum = 0;
@@ -218,7 +219,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ D
     if (t == 0) s_carry += pass_total;
     __syncthreads();
   }
-  if (t == 0) P.tile_base[n] = s_carry;
+  if (t == 0) {
+    P.tile_base[n] = s_carry;
+    if (P.scan_end) *P.scan_end = s_carry;
+  }
 }
 
 template <int S, int B, class E>
@@ -242,7 +246,7 @@ __global__ void __launch_bounds__(B, write_min_blocks<B>())
   uint32_t* col = s_bits + t;
   uint32_t cur_field = 0xffffffffu;
   const LaunchSize LS = launch_size(P);
-  uint64_t g = blockIdx.x;
+  uint64_t g = LS.lo + blockIdx.x;
   TileIn<S> nxt;
   uint32_t nfi = 0;
   if (g < LS.units) {
@@ -315,7 +319,8 @@ cudaError_t launch_persistent(Kern kern, const DecodeParams& p, int B, size_t sm
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   uint64_t grid = static_cast<uint64_t>(per_sm) * num_sms;
   if (grid_cap && grid_cap < grid) grid = grid_cap;
-  if (grid > p.total_units) grid = p.total_units;
+  const uint64_t units = (p.unit_hi ? p.unit_hi : p.total_units) - p.unit_lo;
+  if (grid > units) grid = units;
   if (grid == 0) return cudaSuccess;
   kern<<<static_cast<unsigned>(grid), B, smem, stream>>>(p);
   return cudaGetLastError();
@@ -397,6 +402,42 @@ cudaError_t launch_decode_two_phase(const DecodeParams& p, const LaunchShape& s,
     case 128: return launch_s<128>(p, s, num_sms, stream);
     case 256: return launch_s<256>(p, s, num_sms, stream);
     case 512: return launch_s<512>(p, s, num_sms, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int S>
+cudaError_t launch_count_s(const DecodeParams& p, const LaunchShape& s, int num_sms,
+                           cudaStream_t stream) {
+  switch (s.threads) {
+    case 128: return launch_persistent(k_count<S, 128>, p, 128, count_smem_bytes(s), num_sms, s.grid, stream);
+    case 256: return launch_persistent(k_count<S, 256>, p, 256, count_smem_bytes(s), num_sms, s.grid, stream);
+    case 512: return launch_persistent(k_count<S, 512>, p, 512, count_smem_bytes(s), num_sms, s.grid, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int S>
+cudaError_t launch_write_only_s(const DecodeParams& p, const LaunchShape& s, int num_sms,
+                                cudaStream_t stream) {
+  switch (s.threads) {
+    case 128: return launch_write_sb<S, 128>(p, s, num_sms, stream);
+    case 256: return launch_write_sb<S, 256>(p, s, num_sms, stream);
+    case 512: return launch_write_sb<S, 512>(p, s, num_sms, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_phase(const DecodeParams& p, const LaunchShape& s, Phase phase, int num_sms,
+                         cudaStream_t stream) {
+  if (p.long_cap != s.long_cap || p.window != s.window || s.window < s.S) return cudaErrorInvalidValue;
+  if (phase == Phase::kScan) return launch_scan(p, stream);
+  const bool count = phase == Phase::kCount;
+  switch (s.S) {
+    case 64: return count ? launch_count_s<64>(p, s, num_sms, stream) : launch_write_only_s<64>(p, s, num_sms, stream);
+    case 128: return count ? launch_count_s<128>(p, s, num_sms, stream) : launch_write_only_s<128>(p, s, num_sms, stream);
+    case 256: return count ? launch_count_s<256>(p, s, num_sms, stream) : launch_write_only_s<256>(p, s, num_sms, stream);
+    case 512: return count ? launch_count_s<512>(p, s, num_sms, stream) : launch_write_only_s<512>(p, s, num_sms, stream);
     default: return cudaErrorInvalidValue;
   }
 }

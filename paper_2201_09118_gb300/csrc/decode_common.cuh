@@ -340,14 +340,15 @@ __device__ __forceinline__ Tables make_tables(const FieldDesc& F, uint32_t K, co
 // Field and tile counts of this launch (kernel parameters, or the device-side
 // header of a graph launch).
 struct LaunchSize {
-  uint64_t units;
+  uint64_t units;  // end of the tile range
   uint32_t nfields;
-  bool single;  // the one field is the kernel parameter f0
+  bool single;     // the one field is the kernel parameter f0
+  uint64_t lo;     // start of the tile range
 };
 
 __device__ __forceinline__ LaunchSize launch_size(const DecodeParams& P) {
-  if (P.hdr) return {P.hdr->total_units, P.hdr->nfields, false};
-  return {P.total_units, P.nfields, P.nfields == 1};
+  if (P.hdr) return {P.hdr->total_units, P.hdr->nfields, false, 0};
+  return {P.unit_hi ? P.unit_hi : P.total_units, P.nfields, P.nfields == 1, P.unit_lo};
 }
 
 __device__ __forceinline__ const FieldDesc& field_of(const DecodeParams& P, const LaunchSize& L,

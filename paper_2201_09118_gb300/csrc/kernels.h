@@ -44,8 +44,14 @@ size_t count_smem_bytes(const LaunchShape& s);
 // Bytes per stored codeword count for subsequences of S bits.
 size_t count_bytes_per_subsequence(uint32_t S);
 
-// Decode-and-write kernel alone, for fields whose counts and gap entries are
-// already in place (self-synchronisation writes them).
+// One kernel of the two-phase gap-array decode, for launches over a tile
+// range (p.unit_lo, p.unit_hi) such as the chunks of a pipelined host decode.
+enum class Phase { kCount, kScan, kWrite };
+cudaError_t launch_phase(const DecodeParams& p, const LaunchShape& s, Phase phase, int num_sms,
+                         cudaStream_t stream);
+
+// Tile scan and decode-and-write kernel, for fields whose counts and gap
+// entries are already in place (self-synchronisation writes them).
 cudaError_t launch_write(const DecodeParams& p, const LaunchShape& s, int num_sms,
                          cudaStream_t stream);
 

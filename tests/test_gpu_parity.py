@@ -169,6 +169,33 @@ def test_decode_host(ctx):
     assert hd.HD_OK == 0
 
 
+@pytest.mark.parametrize("shape", [None, {"subseq_bits": 256, "threads": 512, "lut_bits": 14},
+                                   {"subseq_bits": 128, "threads": 128, "lut_bits": 12}])
+def test_decode_host_pipelined(ctx, shape):
+    # large enough to be copied, decoded and copied back in overlapped chunks
+    from paper_2201_09118_gb300 import hd
+    x = synth.laplace_codes(1 << 24, scale=30.0, seed=15)
+    c = oracle.compress(x, 1024, S=128)
+    enc = {"words": c["words"], "gap": c["gap"], "nbits": c["nbits"], "subseq_bits": 128}
+    try:
+        if shape:
+            ctx.set_config(**shape)
+        out = np.full(c["n"] + 32, CANARY, dtype=np.uint16)
+        l0 = ctx.launch_count()
+        got = ctx.decode_host(enc, c["lengths"], c["n"], out=out)
+        assert ctx.launch_count() - l0 > 4  # several chunks
+        assert np.array_equal(got, expect(c))
+        assert np.all(out[c["n"]:] == CANARY)
+        # a count that does not match the stream is reported, nothing written past n
+        out2 = np.full(c["n"] + 32, CANARY, dtype=np.uint16)
+        with pytest.raises(hd.HDError) as e:
+            ctx.decode_host(enc, c["lengths"], c["n"] - 1, out=out2)
+        assert e.value.code == hd.HD_ERR_CORRUPT
+        assert np.all(out2[c["n"] - 1:] == CANARY)
+    finally:
+        ctx.reset_config()
+
+
 def test_batch_mixed_fields(ctx):
     from paper_2201_09118_gb300 import hd
     specs = synth.batch_spec(12, lo=1 << 10, hi=1 << 18, seed=55)
