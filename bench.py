@@ -528,7 +528,7 @@ def run_gpu(args):
                    "autotuned": tuned},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": recorded_traffic("decode_gap", n, launch_gap),
-                     "peak_kind": peak_kind, "kernel": "k_count + k_write",
+                     "peak_kind": peak_kind, "kernel": "k_count + k_scan + k_write",
                      "kernel_ms": kernel_ms, "algorithmic_bytes": nbytes_alg},
         "e2e": {"value": e2e_gbps, "unit": "GB/s",
                 "h2d_bytes_per_step": int(enc["nwords"] * 4 + enc["nsub"] + 1024),

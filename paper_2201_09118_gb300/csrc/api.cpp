@@ -208,7 +208,7 @@ uint64_t pow2_at_least(uint64_t v, uint64_t lo) {
 // Workspace layout of one launch; [0, zero) is cleared by the table kernel.
 struct Layout {
   size_t err = 0, zero = 0, hdr = 0, desc = 0, tab = 0, tile = 0, tbase = 0, count = 0;
-  size_t gap = 0, ta = 0, te = 0, tf = 0, total = 0;
+  size_t gap = 0, ta = 0, te = 0, tf = 0, tg = 0, total = 0;
 };
 
 Layout make_layout(uint32_t nf, uint64_t tiles, uint64_t subs, size_t tab_bytes,
@@ -236,7 +236,8 @@ Layout make_layout(uint32_t nf, uint64_t tiles, uint64_t subs, size_t tab_bytes,
   L.ta = align_up(off, 256);
   L.te = align_up(L.ta + link_bytes, 256);
   L.tf = align_up(L.te + link_bytes, 256);
-  if (self_sync) off = L.tf + tiles;
+  L.tg = align_up(L.tf + tiles, 256);
+  if (self_sync) off = L.tg + tiles;
   L.total = align_up(off, 256);
   return L;
 }
@@ -346,6 +347,7 @@ void make_params(const std::vector<FieldDesc>& descs, char* ws, const Layout& L,
     dp.tile_a = reinterpret_cast<uint8_t*>(ws + L.ta);
     dp.tile_e = reinterpret_cast<uint8_t*>(ws + L.te);
     dp.tile_flag = reinterpret_cast<uint8_t*>(ws + L.tf);
+    dp.tile_guess = reinterpret_cast<uint8_t*>(ws + L.tg);
   }
 }
 
@@ -370,7 +372,7 @@ cudaError_t launch_all(const hd_ctx* c, const hd::PrepParams& pp, const hd::Deco
 }
 
 uint32_t kernels_per_launch(bool self_sync, bool sync_only) {
-  return self_sync ? (sync_only ? 3u : 5u) : 4u;
+  return self_sync ? (sync_only ? 4u : 6u) : 4u;
 }
 
 // Queues a decode of fields that all use the same strategy with direct

@@ -129,6 +129,7 @@ struct DecodeParams {
   uint8_t* tile_a;          // self-synchronisation: start offset each tile assumed
   uint8_t* tile_e;          // self-synchronisation: tile_e[g + 1] = where tile g stopped, minus S
   uint8_t* tile_flag;       // self-synchronisation: 1 = last subsequence overran nbits
+  uint8_t* tile_guess;      // self-synchronisation: guessed start offset of each tile
 };
 
 struct PrepParams {

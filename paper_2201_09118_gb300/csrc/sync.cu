@@ -2,18 +2,25 @@
 // Sec. IV-A): finds the first codeword of every subsequence from the bitstream
 // alone, and counts the codewords of each subsequence on the way.
 //
+//   k_guess one thread per tile guesses where the tile's first codeword
+//           starts by decoding from kLeadBits before the tile's first bit (an
+//           arbitrary position) up to that bit.
 //   k_sync  one tile (B subsequences of S bits) per block pass, no waiting on
-//           other tiles.  A few lanes first re-synchronise the subsequences
-//           just before the tile to guess where its first codeword starts.
-//           Every thread then decodes its subsequence without writing from the
-//           nominal start i*S and stops past the subsequence end.  In rounds,
-//           a thread whose start differs from its predecessor's stop position
-//           walks the new and the old path side by side until they meet at a
-//           common codeword boundary -- from there on both coincide, so the old
-//           stop and count stay valid.  Rounds end when no start changes.
-//           The kernel writes each subsequence's start (as a gap entry) and
-//           codeword count, the tile's count, and the tile's assumed start and
-//           final stop offsets.
+//           other tiles.  Every thread but the first (which takes the tile's
+//           guess) first decodes, without writing, the whole preceding
+//           subsequence from its nominal start up to its own first bit: Huffman
+//           codes re-synchronise within a few codewords, so that lead-in
+//           almost always lands on the true boundary, which becomes the
+//           thread's start.  It then decodes
+//           its own subsequence and stops past its end.  Then, in rounds, a
+//           thread whose start differs from its
+//           predecessor's stop walks the new and the old path side by side
+//           until they meet at a common codeword boundary -- from there on
+//           both coincide, so the old stop and count stay valid.  Rounds run
+//           inside each warp first (shuffles, no block barrier) and then across
+//           warp boundaries; they end when no start changes.  The kernel writes each
+//           subsequence's start (as a gap entry) and codeword count, the
+//           tile's count, and the tile's assumed start and final stop offsets.
 //   k_fix   one block per field checks, in order, that every tile's assumed
 //           start equals its predecessor's stop; a tile where it does not (the
 //           guess was wrong) is synchronised again from the true start, which
@@ -42,10 +49,6 @@ struct CountT<256> {
   using T = uint16_t;
 };
 
-template <int S>
-__host__ __device__ constexpr int presync_lanes() {
-  return 1024 / S < 32 ? 1024 / S : 32;
-}
 
 // Decodes codewords (lengths only) from p while p < end; returns the stop.
 template <int STRIDE>
@@ -89,51 +92,113 @@ __device__ __forceinline__ void repath(const Tables& T, const uint32_t* col, uin
   s = ns;
 }
 
-// Synchronisation rounds over one tile (every thread of the block calls it).
-// Thread 0's predecessor stopped at e_pred (thread 0 starts at e_pred - S).
-// Returns false if the round cap was hit.
+// Rounds inside one warp: lane l > 0 takes lane l-1's stop as its start
+// until no start changes (lane 0 keeps its start).  Returns false if the
+// round cap was hit.
+template <int S, int B>
+__device__ __forceinline__ bool warp_rounds(const Tables& T, const uint32_t* col, bool valid,
+                                            uint32_t end, uint32_t& s, uint32_t& e,
+                                            uint32_t& c) {
+  const int lane = threadIdx.x & 31;
+  for (int round = 0;; ++round) {
+    const uint32_t e_prev = __shfl_up_sync(0xffffffffu, e, 1);
+    const uint32_t ns = (valid && lane) ? e_prev - S : s;
+    const bool changed = ns != s;
+    if (!__any_sync(0xffffffffu, changed)) return true;
+    if (round > 33) return false;
+    if (changed) repath<B>(T, col, end, ns, s, e, c);
+  }
+}
+
+// Synchronisation over one tile (every thread of the block calls it): rounds
+// inside every warp, then rounds over warp boundaries -- lane 0 of warp w takes
+// the stop of warp w-1's last lane (warp 0's lane 0 takes e_pred - S) and, if
+// that changed its start, its warp runs its inner rounds again.  Returns false
+// if a round cap was hit.
 template <int S, int B>
 __device__ __forceinline__ bool sync_rounds(const Tables& T, const uint32_t* col, bool valid,
                                             uint32_t end, uint32_t e_pred, uint32_t& s,
                                             uint32_t& e, uint32_t& c, uint32_t* s_e_last) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  bool ok = warp_rounds<S, B>(T, col, valid, end, s, e, c);
   for (uint32_t round = 0;; ++round) {
-    uint32_t e_prev = __shfl_up_sync(0xffffffffu, e, 1);
     if (lane == 31) s_e_last[warp] = e;
     __syncthreads();
-    if (lane == 0) e_prev = warp ? s_e_last[warp - 1] : e_pred;
     bool changed = false;
-    uint32_t ns = s;
-    if (valid) {
-      ns = e_prev - S;
+    if (lane == 0 && valid) {
+      const uint32_t ns = (warp ? s_e_last[warp - 1] : e_pred) - S;
       changed = ns != s;
+      if (changed) repath<B>(T, col, end, ns, s, e, c);
     }
-    if (!__syncthreads_or(changed)) return true;
-    if (round > B + 1) return false;
-    if (changed) repath<B>(T, col, end, ns, s, e, c);
+    const bool any = __syncthreads_or(changed) != 0;
+    if (!any) return ok;
+    if (round > B / 32 + 1) return false;
+    if (__any_sync(0xffffffffu, changed)) ok &= warp_rounds<S, B>(T, col, valid, end, s, e, c);
   }
 }
 
-// Lanes 0..PRE-1 of warp 0 guess where the tile starting at subsequence i0
-// begins by self-synchronising the PRE subsequences before it.
-template <int S, int PRE>
-__device__ __forceinline__ uint32_t presync_guess(const Tables& T, uint32_t* s_pre,
-                                                  const FieldDesc& F, uint64_t i0) {
-  const int lane = threadIdx.x & 31;
-  const bool on = lane < PRE;
-  uint32_t* col = s_pre + lane;
-  if (on) stage_units<S>(col, F, i0 - PRE + lane, PRE);
-  __syncwarp();
-  uint32_t s = 0, e = 0, c = 0;
-  if (on) e = walk<PRE>(T, col, 0, S, c);
-  for (int round = 0; round < PRE + 2; ++round) {
-    const uint32_t e_prev = __shfl_up_sync(0xffffffffu, e, 1);
-    const uint32_t ns = (on && lane) ? e_prev - S : s;
-    const bool changed = ns != s;
-    if (!__any_sync(0xffffffffu, changed)) break;
-    if (changed) repath<PRE>(T, col, S, ns, s, e, c);
+// Bits the guess kernel decodes before each tile's first bit.
+constexpr uint32_t kLeadBits = 1024;
+constexpr int kGuessThreads = 128;
+
+// One thread per tile: where does the tile's first codeword start?  The
+// thread decodes (lengths only) from kLeadBits before the tile's first bit --
+// an arbitrary position -- up to that bit; Huffman codes re-synchronise within
+// a few codewords, so the walk almost always ends on the true boundary.  A
+// wrong guess only costs time: the link-fix kernel re-synchronises such a
+// tile from its true start.  The lead-in bits are staged in shared memory
+// (one column per thread), the length table is read through the L1 cache
+// (the tiles of one block may belong to different fields).
+template <int B>
+__global__ void __launch_bounds__(kGuessThreads) k_guess(const __grid_constant__ DecodeParams P,
+                                                         uint32_t S) {
+  constexpr int kWords = kLeadBits / 32 + 1;
+  __shared__ uint32_t s_lead[kWords * kGuessThreads];
+  const LaunchSize LS = launch_size(P);
+  const int t = threadIdx.x;
+  uint32_t* col = s_lead + t;
+  for (uint64_t g0 = static_cast<uint64_t>(blockIdx.x) * kGuessThreads; g0 < LS.units;
+       g0 += static_cast<uint64_t>(gridDim.x) * kGuessThreads) {
+    const uint64_t g = g0 + t;
+    uint64_t tl = 0;
+    const FieldDesc* Fp = nullptr;
+    uint32_t first = 0;  // first staged bit relative to the lead-in start
+    if (g < LS.units) {
+      Fp = &field_of(P, LS, find_field(P, LS, g));
+      tl = g - Fp->unit_begin;
+      if (tl > 0 && Fp->table->status == 0) {
+        const uint64_t target = tl * B * S;  // a multiple of 32
+        const uint64_t w0 = target >= kLeadBits ? target / 32 - kLeadBits / 32 : 0;
+        first = static_cast<uint32_t>(target - 32 * w0);
+        for (int k = 0; k < kWords; ++k)
+          col[k * kGuessThreads] = w0 + k < Fp->nwords ? __ldg(Fp->words + w0 + k) : 0u;
+      }
+    }
+    __syncwarp();
+    if (g < LS.units) {
+      uint32_t guess = 0;
+      if (tl > 0 && Fp->table->status == 0) {
+        const TableHeader* H = Fp->table;
+        const uint8_t* len8 =
+            reinterpret_cast<const uint8_t*>(H) + table_len8_off(P.K, Fp->alphabet);
+        const uint32_t shift = 32u - P.K, maxlen = H->maxlen;
+        uint32_t pos = 0;
+        while (pos < first) {
+          const uint32_t w = peek<kGuessThreads>(col, pos);
+          uint32_t L = __ldg(len8 + (w >> shift));
+          if (L & kLen8Walk) {
+            L &= 0x7Fu;
+            while (L <= maxlen && static_cast<uint64_t>(w) >= H->end[L]) ++L;
+            if (L > maxlen) L = 1;  // no codeword here: move on by one bit
+          }
+          pos += L;
+        }
+        guess = pos - first;
+      }
+      P.tile_guess[g] = static_cast<uint8_t>(guess);
+    }
+    __syncwarp();
   }
-  return __shfl_sync(0xffffffffu, e, PRE - 1) - S;
 }
 
 template <int B>
@@ -157,18 +222,17 @@ struct SyncShared {
   uint32_t* s_x;  // [2]: broadcast slots
 };
 
-// Synchronises tile tl of field F given its first start a0 (or, when guess is
-// set, a guessed one), writes the tile's gap entries, counts and totals, and
-// returns the start it used.  tile_flag[g] records whether the field's last
+// Synchronises tile tl of field F given its first start a0 (guessed, or known
+// to be true), writes the tile's gap entries, counts and totals, and returns
+// the start it used.  tile_flag[g] records whether the field's last
 // subsequence ran past nbits; hitting the round cap sets kErrNoSync.
 template <int S, int B>
 __device__ __forceinline__ uint32_t sync_tile(const DecodeParams& P, const FieldDesc& F,
                                               const Tables& T, bool table_ok, uint64_t g,
-                                              bool guess, uint32_t a0, uint32_t* s_bits,
-                                              uint32_t* s_pre, const SyncShared& sh) {
+                                              uint32_t a0, uint32_t* s_bits,
+                                              const SyncShared& sh) {
   using CT = typename CountT<S>::T;
-  constexpr int PRE = presync_lanes<S>();
-  const int t = threadIdx.x, warp = t >> 5;
+  const int t = threadIdx.x;
   uint32_t* col = s_bits + t;
   const uint64_t tl = g - F.unit_begin;
   const uint64_t i = tl * B + t;
@@ -179,14 +243,17 @@ __device__ __forceinline__ uint32_t sync_tile(const DecodeParams& P, const Field
     const uint64_t rem = F.nbits - i * S;
     end = rem < S ? static_cast<uint32_t>(rem) : S;
   }
-  if (guess && warp == 0) {
-    const uint32_t gs = (tl > 0 && table_ok) ? presync_guess<S, PRE>(T, s_pre, F, tl * B) : 0u;
-    if (t == 0) sh.s_x[0] = gs;
-  }
+  __syncthreads();  // the lead-in reads the previous thread's column
   uint32_t s = 0, e = 0, c = 0;
-  if (valid) e = walk<B>(T, col, 0, end, c);
+  if (valid) {
+    // decode the preceding subsequence (whose column ends with this
+    // subsequence's first unit) from its nominal start up to this
+    // subsequence's first bit; its stop is this thread's start
+    uint32_t c_lead = 0;
+    s = t > 0 ? walk<B>(T, col - 1, 0, S, c_lead) - S : a0;
+    e = walk<B>(T, col, s, end, c);
+  }
   __syncthreads();
-  if (guess) a0 = sh.s_x[0];
   uint32_t flags = 0;
   if (!sync_rounds<S, B>(T, col, valid, end, S + a0, s, e, c, sh.s_e_last)) flags |= 2u;
   if (valid && i + 1 == F.nsub && e != end) flags |= 1u;
@@ -210,12 +277,9 @@ __device__ __forceinline__ uint32_t sync_tile(const DecodeParams& P, const Field
 
 template <int S, int B>
 __global__ void __launch_bounds__(B) k_sync(const __grid_constant__ DecodeParams P) {
-  constexpr int W = S / 32 + 1;
-  constexpr int PRE = presync_lanes<S>();
   extern __shared__ __align__(16) unsigned char smem[];
   uint8_t* s_lut = smem;  // length table
   uint32_t* s_bits = reinterpret_cast<uint32_t*>(smem + lut_bytes(Lut::k8, P.K));
-  uint32_t* s_pre = s_bits + W * B;
   __shared__ uint64_t s_end[34];
   __shared__ uint32_t s_base[34];
   __shared__ uint32_t s_meta[3];
@@ -236,7 +300,7 @@ __global__ void __launch_bounds__(B) k_sync(const __grid_constant__ DecodeParams
       __syncthreads();
     }
     const Tables T = make_tables(F, P.K, s_lut, s_end, s_base, s_meta, nullptr, 0);
-    sync_tile<S, B>(P, F, T, s_meta[1] == 0, g, true, 0u, s_bits, s_pre, sh);
+    sync_tile<S, B>(P, F, T, s_meta[1] == 0, g, P.tile_guess[g], s_bits, sh);
   }
 }
 
@@ -281,12 +345,9 @@ __device__ __forceinline__ uint64_t first_broken(const DecodeParams& P, uint64_t
 // checks that the field's last subsequence ended at nbits.
 template <int S, int B>
 __global__ void __launch_bounds__(B) k_fix(const __grid_constant__ DecodeParams P) {
-  constexpr int W = S / 32 + 1;
-  constexpr int PRE = presync_lanes<S>();
   extern __shared__ __align__(16) unsigned char smem[];
   uint8_t* s_lut = smem;  // length table
   uint32_t* s_bits = reinterpret_cast<uint32_t*>(smem + lut_bytes(Lut::k8, P.K));
-  uint32_t* s_pre = s_bits + W * B;
   __shared__ uint64_t s_end[34];
   __shared__ uint32_t s_base[34];
   __shared__ uint32_t s_meta[3];
@@ -310,7 +371,7 @@ __global__ void __launch_bounds__(B) k_fix(const __grid_constant__ DecodeParams 
     while (table_ok && cursor < g1) {
       const uint64_t gb = first_broken<B>(P, cursor, g1, &s_first);
       if (gb >= g1) break;
-      sync_tile<S, B>(P, F, T, table_ok, gb, false, P.tile_e[gb], s_bits, s_pre, sh);
+      sync_tile<S, B>(P, F, T, table_ok, gb, P.tile_e[gb], s_bits, sh);
       cursor = gb + 1;
     }
     if (threadIdx.x == 0) {
@@ -339,6 +400,11 @@ cudaError_t launch_sb(const DecodeParams& p, const LaunchShape& s, int num_sms,
   if (s.grid && s.grid < grid) grid = s.grid;
   if (grid > p.total_units) grid = p.total_units;
   if (grid == 0) return cudaSuccess;
+  const uint64_t gblocks = (p.total_units + kGuessThreads - 1) / kGuessThreads;
+  k_guess<B><<<static_cast<unsigned>(gblocks < 8192 ? gblocks : 8192), kGuessThreads, 0, stream>>>(
+      p, S);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   ks<<<static_cast<unsigned>(grid), B, smem, stream>>>(p);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -363,8 +429,7 @@ cudaError_t launch_s(const DecodeParams& p, const LaunchShape& s, int num_sms,
 
 size_t sync_smem_bytes(const LaunchShape& s) {
   const size_t W = s.S / 32 + 1;
-  const size_t pre = 1024 / s.S < 32 ? 1024 / s.S : 32;
-  const size_t b = dev::lut_bytes(dev::Lut::k8, s.K) + W * s.threads * 4 + W * pre * 4;
+  const size_t b = dev::lut_bytes(dev::Lut::k8, s.K) + W * s.threads * 4;
   return (b + 15) & ~static_cast<size_t>(15);
 }
 
