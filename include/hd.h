@@ -87,6 +87,12 @@ int hd_encode(const uint16_t* codes, uint64_t n, const uint8_t* lengths, uint32_
               uint32_t subseq_bits, uint32_t* words_out, uint64_t words_cap, uint8_t* gap_out,
               uint64_t gap_cap, hd_stream_info* info);
 
+/* Code lengths of an optimal prefix code for the symbol counts freq[alphabet]
+ * (as hd_build_codebook, from counts instead of symbols, e.g. those of
+ * hd_histogram_device).  Host memory.  Errors as hd_build_codebook. */
+int hd_build_codebook_freq(const uint64_t* freq, uint32_t alphabet, uint32_t max_len,
+                           uint8_t* lengths_out);
+
 /* ---- device context ---------------------------------------------------- */
 
 typedef struct hd_ctx hd_ctx;
@@ -297,6 +303,28 @@ int hd_serve_completed(hd_server* srv, uint64_t* tickets, uint32_t cap, uint32_t
  * memory, so outputs must be released meanwhile if the budget is short. */
 int hd_serve_drain(hd_server* srv);
 int hd_serve_stats(hd_server* srv, hd_serve_stats_t* out);
+
+/* ---- GPU encoding (the step before the decoder) ------------------------- */
+
+/* Symbol counts of d_codes[0 .. n) (device) into freq_out[alphabet] (host).
+ * Synchronous.  HD_ERR_SYMBOL if a code is >= alphabet. */
+int hd_histogram_device(hd_ctx* ctx, const uint16_t* d_codes, uint64_t n, uint32_t alphabet,
+                        uint64_t* freq_out, void* stream);
+
+/* GPU counterpart of hd_encode, bit-identical to it: canonical-Huffman
+ * encodes d_codes[0 .. n) (device, 2-byte aligned) with the code lengths
+ * `lengths` (HOST, [alphabet]) into d_words (device, 4-byte aligned) in the
+ * stream format above and, when d_gap is not NULL, writes the gap array of
+ * subseq_bits-bit subsequences (Sec. III-C) into d_gap.  Symbol tiles are
+ * sized by a per-tile bit count and a scan, then every codeword is OR-ed into
+ * place in shared memory and the gap entry of each subsequence is written by
+ * the thread placing its first codeword.  Synchronous (the stream length is
+ * needed to check capacities); `info` always receives the sizes.  Errors as
+ * hd_encode (HD_ERR_CAPACITY, HD_ERR_SYMBOL, HD_ERR_ARG), HD_ERR_CUDA. */
+int hd_encode_device(hd_ctx* ctx, const uint16_t* d_codes, uint64_t n, const uint8_t* lengths,
+                     uint32_t alphabet, uint32_t subseq_bits, uint32_t* d_words,
+                     uint64_t words_cap, uint8_t* d_gap, uint64_t gap_cap, hd_stream_info* info,
+                     void* stream);
 
 /* Kernel timing: when enabled, the context records CUDA events around every
  * main decode kernel it launches.  hd_kernel_time waits for them and returns

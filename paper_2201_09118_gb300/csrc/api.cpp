@@ -1123,6 +1123,108 @@ int hd_decode_host(hd_ctx* c, const hd_field* f, uint16_t* host_out, void* strea
   return map_err_bits(all);
 }
 
+int hd_histogram_device(hd_ctx* c, const uint16_t* d_codes, uint64_t n, uint32_t alphabet,
+                        uint64_t* freq_out, void* stream) {
+  if (!c || !freq_out || (n && !d_codes)) return HD_ERR_ARG;
+  if (alphabet < 1 || alphabet > 65536) return HD_ERR_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = ensure_ws(c, 256 + 8ull * alphabet);
+  if (rc) return rc;
+  char* ws = c->ws;
+  uint32_t err = 0;
+  auto* hist = reinterpret_cast<unsigned long long*>(ws + 256);
+  if (cudaMemsetAsync(ws, 0, 256 + 8ull * alphabet, st) != cudaSuccess ||
+      hd::launch_histogram(d_codes, n, alphabet, hist, reinterpret_cast<uint32_t*>(ws),
+                           c->num_sms, st) != cudaSuccess ||
+      cudaMemcpyAsync(freq_out, hist, 8ull * alphabet, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(&err, ws, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return HD_ERR_CUDA;
+  }
+  c->launches += n ? 1 : 0;
+  c->err_count = 0;
+  return err ? HD_ERR_SYMBOL : HD_OK;
+}
+
+int hd_encode_device(hd_ctx* c, const uint16_t* d_codes, uint64_t n, const uint8_t* lengths,
+                     uint32_t alphabet, uint32_t subseq_bits, uint32_t* d_words,
+                     uint64_t words_cap, uint8_t* d_gap, uint64_t gap_cap, hd_stream_info* info,
+                     void* stream) {
+  if (!c || !info || !lengths || (n && !d_codes)) return HD_ERR_ARG;
+  if (alphabet < 1 || alphabet > 65536) return HD_ERR_ARG;
+  if (subseq_bits != 64 && subseq_bits != 128 && subseq_bits != 256) return HD_ERR_ARG;
+  if (d_codes && (reinterpret_cast<uintptr_t>(d_codes) & 1u)) return HD_ERR_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  std::vector<uint32_t> cw(alphabet);
+  int rc = hd::canonical_codewords(lengths, alphabet, cw.data());
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint64_t tiles = hd::encode_tiles(n);
+  // workspace: error word | lengths | codewords | tile bits | tile offsets
+  const size_t err_off = 0;
+  const size_t len_off = 256;
+  const size_t cw_off = align_up(len_off + alphabet, 256);
+  const size_t tb_off = align_up(cw_off + 4ull * alphabet, 256);
+  const size_t to_off = align_up(tb_off + 4ull * tiles, 256);
+  rc = ensure_ws(c, to_off + 8ull * (tiles + 1));
+  if (rc) return rc;
+  char* ws = c->ws;
+  c->err_count = 0;  // hd_status does not report encodes
+  hd::EncodeParams e{};
+  e.codes = d_codes;
+  e.n = n;
+  e.lengths = reinterpret_cast<const uint8_t*>(ws + len_off);
+  e.codewords = reinterpret_cast<const uint32_t*>(ws + cw_off);
+  e.alphabet = alphabet;
+  e.subseq_bits = subseq_bits;
+  e.tiles = tiles;
+  e.tile_bits = reinterpret_cast<uint32_t*>(ws + tb_off);
+  e.tile_off = reinterpret_cast<uint64_t*>(ws + to_off);
+  e.err = reinterpret_cast<uint32_t*>(ws + err_off);
+  uint64_t nbits = 0;
+  uint32_t err = 0;
+  if (cudaMemsetAsync(ws + err_off, 0, 16, st) != cudaSuccess ||
+      cudaMemcpyAsync(ws + len_off, lengths, alphabet, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(ws + cw_off, cw.data(), 4ull * alphabet, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      hd::launch_encode_count(e, c->num_sms, st) != cudaSuccess)
+    return HD_ERR_CUDA;
+  c->launches += tiles ? 2 : 0;
+  if ((tiles && cudaMemcpyAsync(&nbits, ws + to_off + 8 * tiles, 8, cudaMemcpyDeviceToHost, st) !=
+                    cudaSuccess) ||
+      cudaMemcpyAsync(&err, ws + err_off, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return HD_ERR_CUDA;
+  }
+  if (err) return HD_ERR_SYMBOL;
+  const uint32_t S = subseq_bits;
+  info->nbits = nbits;
+  info->nsub = (nbits + S - 1) / S;
+  info->nwords = hd::stream_words(nbits, S);
+  if (!d_words || words_cap < info->nwords) return HD_ERR_CAPACITY;
+  if (d_gap && gap_cap < info->nsub) return HD_ERR_CAPACITY;
+  if (reinterpret_cast<uintptr_t>(d_words) & 3u) return HD_ERR_ARG;
+  e.words = d_words;
+  e.gap = d_gap;
+  e.nsub = info->nsub;
+  if (cudaMemsetAsync(d_words, 0, 4ull * info->nwords, st) != cudaSuccess ||
+      hd::launch_encode_write(e, c->num_sms, st) != cudaSuccess)
+    return HD_ERR_CUDA;
+  c->launches += tiles ? 1 : 0;
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return HD_ERR_CUDA;
+  }
+  return HD_OK;
+}
+
 int hd_profile(hd_ctx* c, int enable) {
   if (!c) return HD_ERR_ARG;
   std::lock_guard<std::mutex> lk(c->mu);

@@ -125,6 +125,13 @@ int build_code_lengths(const uint64_t* freq, uint32_t alphabet, uint32_t max_len
 
 }  // namespace hd
 
+extern "C" int hd_build_codebook_freq(const uint64_t* freq, uint32_t alphabet, uint32_t max_len,
+                                      uint8_t* lengths_out) {
+  if (alphabet < 2 || alphabet > 65536 || max_len < 1 || max_len > 32) return HD_ERR_ARG;
+  if (!freq || !lengths_out) return HD_ERR_ARG;
+  return hd::build_code_lengths(freq, alphabet, max_len, lengths_out);
+}
+
 extern "C" int hd_build_codebook(const uint16_t* codes, uint64_t n, uint32_t alphabet,
                                  uint32_t max_len, uint8_t* lengths_out) {
   if (alphabet < 2 || alphabet > 65536 || max_len < 1 || max_len > 32) return HD_ERR_ARG;

@@ -144,6 +144,24 @@ struct PrepParams {
   uint32_t zero_blocks;
 };
 
+// GPU encoder (encode_gpu.cu).
+struct EncodeParams {
+  const uint16_t* codes;      // symbols [n]
+  uint64_t n;
+  const uint8_t* lengths;     // code lengths [alphabet]
+  const uint32_t* codewords;  // canonical codewords [alphabet], right-aligned
+  uint32_t alphabet;
+  uint32_t subseq_bits;       // S of the gap array
+  uint64_t tiles;             // symbol tiles
+  uint32_t* tile_bits;        // code bits per tile
+  uint64_t* tile_off;         // stream offset of each tile [tiles + 1]
+  uint64_t* total_out;        // stream length (may be NULL)
+  uint32_t* words;            // stream, zeroed before the write kernel
+  uint8_t* gap;               // gap array [nsub] or NULL
+  uint64_t nsub;
+  uint32_t* err;              // bit 0: a symbol without a code
+};
+
 // Look-back state word: flag in bits 62..63, value in bits 0..61.
 constexpr uint64_t kStateAgg = 1ull << 62;
 constexpr uint64_t kStateInc = 2ull << 62;

@@ -163,66 +163,12 @@ __global__ void __launch_bounds__(B, count_min_blocks<B>())
   }
 }
 
-// One block of kScanThreads: tile_base[g] = sum of tile_total[j] for j < g,
-// over the tiles of the launch (g in [unit_lo, units]; a range that starts
-// later continues from tile_base[unit_lo]).  The tiles are taken in
-// passes of kScanThreads * kScanPer; in a pass each thread owns kScanPer
-// consecutive tiles, whose totals it loads at once (independent loads), and a
-// block scan of the per-thread sums gives each run's first base.
-constexpr int kScanThreads = 1024;
-constexpr int kScanPer = 16;
-
+// One block: tile_base[g] = sum of tile_total[j] for j < g over the tiles of
+// the launch (g in [unit_lo, units]; a range that starts later continues from
+// tile_base[unit_lo]).
 __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ DecodeParams P) {
-  __shared__ uint64_t s_part[kScanThreads / 32];
-  __shared__ uint64_t s_carry;
   const LaunchSize LS = launch_size(P);
-  const uint64_t n = LS.units;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  // a range that does not start at tile 0 continues the previous range's sum
-  if (t == 0) s_carry = LS.lo ? P.tile_base[LS.lo] : 0ull;
-  __syncthreads();
-  for (uint64_t p0 = LS.lo; p0 < n; p0 += static_cast<uint64_t>(kScanThreads) * kScanPer) {
-    const uint64_t a = p0 + static_cast<uint64_t>(t) * kScanPer;
-    uint32_t v[kScanPer];
-    uint64_t sum = 0;
-#pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-      v[k] = a + k < n ? P.tile_total[a + k] : 0u;
-      sum += v[k];
-    }
-    uint64_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += u;
-    }
-    if (lane == 31) s_part[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      uint64_t x = s_part[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t u = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += u;
-      }
-      s_part[lane] = x;
-    }
-    __syncthreads();
-    uint64_t run = s_carry + (warp ? s_part[warp - 1] : 0ull) + incl - sum;
-#pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-      if (a + k < n) P.tile_base[a + k] = run;
-      run += v[k];
-    }
-    const uint64_t pass_total = s_part[kScanThreads / 32 - 1];
-    __syncthreads();
-    if (t == 0) s_carry += pass_total;
-    __syncthreads();
-  }
-  if (t == 0) {
-    P.tile_base[n] = s_carry;
-    if (P.scan_end) *P.scan_end = s_carry;
-  }
+  scan_totals(P.tile_total, P.tile_base, LS.lo, LS.units, P.scan_end);
 }
 
 template <int S, int B, class E>

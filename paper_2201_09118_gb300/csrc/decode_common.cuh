@@ -400,6 +400,67 @@ __device__ __forceinline__ void stage_units(uint32_t* col, const FieldDesc& F, u
   col[U * stride] = (w0 + U < F.nwords) ? __ldg(src + U) : 0u;
 }
 
+// Exclusive scan of 32-bit totals into 64-bit bases by one block of
+// kScanThreads: base[j] = base[lo] + sum of total[k] for lo <= k < j, for j in
+// [lo, hi], where base[lo] is read as 0 when lo == 0 (a later range continues
+// the previous one).  end_out (may be NULL) also receives base[hi].  The
+// totals are taken in passes of kScanThreads * kScanPer; in a pass each thread
+// owns kScanPer consecutive totals, which it loads at once (independent
+// loads), and a block scan of the per-thread sums gives each run's first base.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 16;
+
+__device__ __forceinline__ void scan_totals(const uint32_t* total, uint64_t* base, uint64_t lo,
+                                            uint64_t hi, uint64_t* end_out) {
+  __shared__ uint64_t s_part[kScanThreads / 32];
+  __shared__ uint64_t s_carry;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (t == 0) s_carry = lo ? base[lo] : 0ull;
+  __syncthreads();
+  for (uint64_t p0 = lo; p0 < hi; p0 += static_cast<uint64_t>(kScanThreads) * kScanPer) {
+    const uint64_t a = p0 + static_cast<uint64_t>(t) * kScanPer;
+    uint32_t v[kScanPer];
+    uint64_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      v[k] = a + k < hi ? total[a + k] : 0u;
+      sum += v[k];
+    }
+    uint64_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) s_part[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      uint64_t x = s_part[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t u = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += u;
+      }
+      s_part[lane] = x;
+    }
+    __syncthreads();
+    uint64_t run = s_carry + (warp ? s_part[warp - 1] : 0ull) + incl - sum;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      if (a + k < hi) base[a + k] = run;
+      run += v[k];
+    }
+    const uint64_t pass_total = s_part[kScanThreads / 32 - 1];
+    __syncthreads();
+    if (t == 0) s_carry += pass_total;
+    __syncthreads();
+  }
+  if (t == 0) {
+    base[hi] = s_carry;
+    if (end_out) *end_out = s_carry;
+  }
+}
+
 // The units of one subsequence held in registers, so that a tile's loads can
 // be issued while the previous tile is still being decoded.
 template <int S>

@@ -73,4 +73,13 @@ size_t sync_smem_bytes(const LaunchShape& s);
 cudaError_t launch_decode_single_pass(const DecodeParams& p, const LaunchShape& s, int num_sms,
                                       cudaStream_t stream);
 
+// GPU encoder: symbol tiles of a stream of n symbols; per-tile code bits and
+// their scan (tile_off[tiles] = stream bits); then the stream and gap array.
+uint64_t encode_tiles(uint64_t n);
+cudaError_t launch_histogram(const uint16_t* codes, uint64_t n, uint32_t alphabet,
+                             unsigned long long* hist, uint32_t* err, int num_sms,
+                             cudaStream_t stream);
+cudaError_t launch_encode_count(const EncodeParams& e, int num_sms, cudaStream_t stream);
+cudaError_t launch_encode_write(const EncodeParams& e, int num_sms, cudaStream_t stream);
+
 }  // namespace hd

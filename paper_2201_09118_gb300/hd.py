@@ -82,6 +82,11 @@ _SIGS = {
     "hd_encode": ([_P, ctypes.c_uint64, _P, ctypes.c_uint32, ctypes.c_uint32, _P,
                    ctypes.c_uint64, _P, ctypes.c_uint64, ctypes.POINTER(hd_stream_info)],
                   ctypes.c_int),
+    "hd_build_codebook_freq": ([_P, ctypes.c_uint32, ctypes.c_uint32, _P], ctypes.c_int),
+    "hd_histogram_device": ([_P, _P, ctypes.c_uint64, ctypes.c_uint32, _P, _P], ctypes.c_int),
+    "hd_encode_device": ([_P, _P, ctypes.c_uint64, _P, ctypes.c_uint32, ctypes.c_uint32, _P,
+                          ctypes.c_uint64, _P, ctypes.c_uint64, ctypes.POINTER(hd_stream_info),
+                          _P], ctypes.c_int),
     "hd_ctx_create": ([ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
     "hd_ctx_destroy": ([_P], ctypes.c_int),
     "hd_set_config": ([_P, ctypes.POINTER(hd_config)], ctypes.c_int),
@@ -172,6 +177,14 @@ def hd_build_codebook(codes: np.ndarray, alphabet: int, max_len: int = 32) -> np
     out = np.zeros(alphabet, dtype=np.uint8)
     _check("hd_build_codebook",
            load().hd_build_codebook(_np_ptr(codes), codes.size, alphabet, max_len, _np_ptr(out)))
+    return out
+
+
+def hd_build_codebook_freq(freq: np.ndarray, max_len: int = 32) -> np.ndarray:
+    freq = np.ascontiguousarray(freq, dtype=np.uint64)
+    out = np.zeros(freq.size, dtype=np.uint8)
+    _check("hd_build_codebook_freq",
+           load().hd_build_codebook_freq(_np_ptr(freq), freq.size, max_len, _np_ptr(out)))
     return out
 
 
@@ -305,6 +318,39 @@ class Context:
         _check("hd_graph_stats", self._lib.hd_graph_stats(self.handle, ctypes.byref(cap),
                                                           ctypes.byref(cached)))
         return cap.value, cached.value
+
+    def histogram(self, codes, alphabet: int, stream=None) -> np.ndarray:
+        """Symbol counts of a device int16/uint16 tensor (hd_histogram_device)."""
+        freq = np.zeros(alphabet, dtype=np.uint64)
+        _check("hd_histogram_device", self._lib.hd_histogram_device(
+            self.handle, codes.data_ptr(), codes.numel(), alphabet, _np_ptr(freq),
+            _stream_handle(stream)))
+        return freq
+
+    def encode(self, codes, lengths: np.ndarray, subseq_bits: int = 128, with_gap: bool = True,
+               stream=None) -> dict:
+        """GPU encode of a device tensor of symbols (hd_encode_device); returns
+        device tensors 'words' (int32 view of the uint32 units) and 'gap' (or
+        None) with 'nbits', 'nwords', 'nsub'."""
+        import torch
+        lengths = np.ascontiguousarray(lengths, dtype=np.uint8)
+        info = hd_stream_info()
+        rc = self._lib.hd_encode_device(self.handle, codes.data_ptr(), codes.numel(),
+                                        _np_ptr(lengths), lengths.size, subseq_bits, None, 0,
+                                        None, 0, ctypes.byref(info), _stream_handle(stream))
+        if rc not in (HD_OK, HD_ERR_CAPACITY):
+            raise HDError("hd_encode_device", rc)
+        words = torch.empty(max(1, info.nwords), dtype=torch.int32, device=codes.device)
+        gap = (torch.empty(max(1, info.nsub), dtype=torch.uint8, device=codes.device)
+               if with_gap else None)
+        _check("hd_encode_device", self._lib.hd_encode_device(
+            self.handle, codes.data_ptr(), codes.numel(), _np_ptr(lengths), lengths.size,
+            subseq_bits, words.data_ptr(), words.numel(),
+            gap.data_ptr() if gap is not None else None, gap.numel() if gap is not None else 0,
+            ctypes.byref(info), _stream_handle(stream)))
+        return {"words": words[:info.nwords], "gap": None if gap is None else gap[:info.nsub],
+                "nbits": int(info.nbits), "nwords": int(info.nwords), "nsub": int(info.nsub),
+                "subseq_bits": subseq_bits}
 
     def batch_status(self, nf: int, stream=None):
         st = np.zeros(max(1, nf), dtype=np.int32)

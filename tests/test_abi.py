@@ -83,3 +83,11 @@ def test_encoder_errors():
     with pytest.raises(hd.HDError) as e:
         hd.hd_build_codebook(np.array([9], np.uint16), 8)
     assert e.value.code == hd.HD_ERR_SYMBOL
+
+
+def test_codebook_from_counts_matches_codebook_from_symbols():
+    x = synth.laplace_codes(100000, scale=12.0, seed=9)
+    freq = np.bincount(x, minlength=1024).astype(np.uint64)
+    assert np.array_equal(hd.hd_build_codebook_freq(freq, 32), hd.hd_build_codebook(x, 1024, 32))
+    with pytest.raises(hd.HDError):
+        hd.hd_build_codebook_freq(np.zeros(1, np.uint64), 32)  # alphabet < 2
