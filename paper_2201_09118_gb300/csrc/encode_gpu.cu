@@ -7,10 +7,12 @@
 //                code set the error word.
 //   (scan)       tile bit offsets = exclusive scan of the tile totals.
 //   k_enc_write  one block per tile: a block scan of the threads' bit counts
-//                places every codeword; codewords are OR-ed into the tile's
-//                words in shared memory, which are then stored (the two words a
-//                tile may share with its neighbours with atomicOr on the zeroed
-//                stream).  The thread that places a codeword starting at or
+//                places every thread's codewords; each thread assembles its
+//                codewords in a 64-bit register and emits whole words into the
+//                tile's words in shared memory (OR for the first and last word,
+//                which it may share with its neighbours), which are then stored
+//                (the two words a tile may share with its neighbour tiles with
+//                atomicOr on the zeroed stream).  The thread that places a codeword starting at or
 //                after a subsequence boundary j*S, with the previous codeword
 //                starting before it, writes gap[j]; the end of the stream
 //                closes the last open subsequence.
@@ -47,24 +49,35 @@ __device__ __forceinline__ void load_symbols(const uint16_t* codes, uint64_t n, 
   }
 }
 
+// Shared-memory copies of the code tables for alphabets up to kEncSmemAlphabet.
+constexpr uint32_t kEncSmemAlphabet = 4096;
+
 __global__ void __launch_bounds__(kEncThreads) k_enc_count(const __grid_constant__ EncodeParams E) {
   __shared__ uint32_t s_warp[kEncThreads / 32];
+  __shared__ uint8_t s_len[kEncSmemAlphabet];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const bool smem_tab = E.alphabet <= kEncSmemAlphabet;
+  if (smem_tab)
+    for (uint32_t k = t; k < E.alphabet; k += kEncThreads) s_len[k] = E.lengths[k];
+  __syncthreads();
+  const uint8_t* lens = smem_tab ? s_len : E.lengths;
+  const uint32_t amax = E.alphabet - 1;
   for (uint64_t tile = blockIdx.x; tile < E.tiles; tile += gridDim.x) {
     const uint64_t i0 = tile * kEncTile + static_cast<uint64_t>(t) * kEncPer;
     uint32_t x[kEncPer];
     load_symbols(E.codes, E.n, i0, x);
-    uint32_t bits = 0;
-    bool bad = false;
+    const uint32_t m = i0 < E.n ? static_cast<uint32_t>(E.n - i0 < kEncPer ? E.n - i0 : kEncPer) : 0u;
+    uint32_t bits = 0, xmax = 0, lmin = 32;
 #pragma unroll
     for (int k = 0; k < kEncPer; ++k) {
-      if (i0 + k < E.n) {
-        const uint32_t L = x[k] < E.alphabet ? __ldg(E.lengths + x[k]) : 0u;
-        bad |= L == 0;
+      if (k < static_cast<int>(m)) {
+        const uint32_t L = lens[min(x[k], amax)];
+        xmax = max(xmax, x[k]);
+        lmin = min(lmin, L);
         bits += L;
       }
     }
-    if (bad) atomicOr(E.err, 1u);
+    if (m && (xmax > amax || lmin == 0)) atomicOr(E.err, 1u);
 #pragma unroll
     for (int o = 16; o; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
     if (lane == 0) s_warp[warp] = bits;
@@ -86,8 +99,19 @@ __global__ void __launch_bounds__(kEncThreads) k_enc_write(const __grid_constant
   // a tile of kEncTile codewords of at most 32 bits spans at most kEncTile + 1 words
   __shared__ uint32_t s_w[kEncTile + 2];
   __shared__ uint32_t s_warp[kEncThreads / 32];
+  __shared__ uint32_t s_cw[kEncSmemAlphabet];
+  __shared__ uint8_t s_len[kEncSmemAlphabet];
   const int t = threadIdx.x;
-  const uint64_t S = E.subseq_bits;
+  const uint32_t lgS = 31u - __clz(E.subseq_bits);  // S is a power of two
+  const bool smem_tab = E.alphabet <= kEncSmemAlphabet;
+  if (smem_tab)
+    for (uint32_t k = t; k < E.alphabet; k += kEncThreads) {
+      s_len[k] = E.lengths[k];
+      s_cw[k] = E.codewords[k];
+    }
+  __syncthreads();
+  const uint8_t* lens = smem_tab ? s_len : E.lengths;
+  const uint32_t* cws = smem_tab ? s_cw : E.codewords;
   for (uint64_t tile = blockIdx.x; tile < E.tiles; tile += gridDim.x) {
     const uint64_t base = E.tile_off[tile];
     const uint64_t tile_end = E.tile_off[tile + 1];
@@ -101,44 +125,66 @@ __global__ void __launch_bounds__(kEncThreads) k_enc_write(const __grid_constant
     uint32_t bits = 0;
 #pragma unroll
     for (int k = 0; k < kEncPer; ++k) {
-      len[k] = (i0 + k < E.n && x[k] < E.alphabet) ? __ldg(E.lengths + x[k]) : 0u;
+      len[k] = (i0 + k < E.n && x[k] < E.alphabet) ? lens[x[k]] : 0u;
       bits += len[k];
     }
     uint32_t total;
     const uint32_t excl = block_excl_scan<kEncThreads>(bits, s_warp, &total);
-    // length of the codeword before this thread's first one
-    uint32_t prev_len = 0;
-    if (i0 > 0 && i0 - 1 < E.n) {
-      const uint32_t xp = __ldg(E.codes + i0 - 1);
-      prev_len = xp < E.alphabet ? __ldg(E.lengths + xp) : 0u;
-    }
-    uint64_t off = base + excl;               // stream position of the next codeword
-    uint32_t r = static_cast<uint32_t>(off - (word0 << 5));  // its position in s_w
+    const uint64_t off0 = base + excl;  // stream position of the thread's first codeword
+    if (bits) {
+      // assemble the thread's codewords in a 64-bit register, most significant
+      // bit first, and emit whole words; the first and the last word may be
+      // shared with the neighbouring threads (OR), the others are its own
+      uint32_t r = static_cast<uint32_t>(off0 - (word0 << 5));
+      uint32_t q = r >> 5;
+      uint32_t nacc = r & 31;
+      uint64_t acc = 0;
+      bool first = true;
 #pragma unroll
-    for (int k = 0; k < kEncPer; ++k) {
-      const uint32_t L = len[k];
-      if (L) {
-        // the codeword, left-aligned in 32 bits
-        const uint32_t cw = __ldg(E.codewords + x[k]) << (32 - L);
-        const uint32_t q = r >> 5, sh = r & 31;
-        atomicOr(&s_w[q], cw >> sh);
-        if (sh + L > 32) atomicOr(&s_w[q + 1], cw << (32 - sh));
-        if (E.gap) {
-          // subsequence j whose boundary j*S lies in (previous start, this start]
-          const uint64_t j = off / S;
-          const uint64_t prev = i0 + k > 0 ? off - prev_len : 0;
-          if (j * S <= off && (i0 + k == 0 || j * S > prev) && j < E.nsub)
-            E.gap[j] = static_cast<uint8_t>(off - j * S);
+      for (int k = 0; k < kEncPer; ++k) {
+        const uint32_t L = len[k];
+        if (L) {
+          acc |= static_cast<uint64_t>(cws[x[k]]) << (64 - nacc - L);
+          nacc += L;
+          if (nacc >= 32) {
+            const uint32_t w = static_cast<uint32_t>(acc >> 32);
+            if (first) atomicOr(&s_w[q], w);
+            else s_w[q] = w;
+            first = false;
+            ++q;
+            acc <<= 32;
+            nacc -= 32;
+          }
         }
-        prev_len = L;
-        off += L;
-        r += L;
-        if (E.gap && i0 + k + 1 == E.n) {
-          // the end of the stream closes the last subsequence that starts
-          // after the last codeword's start
-          const uint64_t last = off - L;
-          const uint64_t j = (last / S) + 1;
-          if (j < E.nsub && j * S <= off) E.gap[j] = static_cast<uint8_t>(off - j * S);
+      }
+      // a last partial word is shared with the next thread's first one; a
+      // range that ends on a word boundary left no partial word
+      if (nacc) atomicOr(&s_w[q], static_cast<uint32_t>(acc >> 32));
+      if (E.gap) {
+        // gap[j] for every subsequence boundary j*S in (previous start, start]
+        // of one of this thread's codewords; the end of the stream closes the
+        // last subsequence
+        uint64_t prev = 0;
+        if (i0 > 0) {
+          const uint32_t xp = __ldg(E.codes + i0 - 1);
+          prev = off0 - (xp < E.alphabet ? lens[xp] : 0u);
+        }
+        uint64_t off = off0;
+#pragma unroll
+        for (int k = 0; k < kEncPer; ++k) {
+          const uint32_t L = len[k];
+          if (L) {
+            const uint64_t j = off >> lgS;
+            if ((i0 + k == 0 || (j << lgS) > prev) && j < E.nsub)
+              E.gap[j] = static_cast<uint8_t>(off - (j << lgS));
+            prev = off;
+            off += L;
+            if (i0 + k + 1 == E.n) {
+              const uint64_t je = (prev >> lgS) + 1;
+              if (je < E.nsub && (je << lgS) <= off)
+                E.gap[je] = static_cast<uint8_t>(off - (je << lgS));
+            }
+          }
         }
       }
     }
