@@ -287,6 +287,56 @@ def run_encode(hd, torch, ctx, codes, lengths, enc, stream, flush, steps: int = 
             "timing": "wall clock around the synchronous call (incl. its length read-back)"}
 
 
+def mixed_cr_workload(n_seg: int = 32, seg: int = 1 << 21, seed: int = 1005):
+    """A 1D field whose compressibility changes along it (segments quantized at
+    error bounds 1e-2 .. 1e-6), for the window-class ablation."""
+    import synth
+    ebs = [1e-2, 1e-6, 1e-3, 1e-5, 1e-2, 1e-4, 1e-6, 1e-2]
+    return np.concatenate([synth.smooth_codes_1d(seg, ebs[k % 8], alphabet=1024, seed=seed + k)
+                           for k in range(n_seg)])
+
+
+def run_cr_ablation(hd, torch, ctx_dev, stream, flush, codes, steps: int = 5):
+    """Algorithm 2 (per-tile compression-ratio window classes) against the
+    autotuned single-window shape on a field of mixed compressibility."""
+    n = codes.size
+    lengths = hd.hd_build_codebook(codes, 1024, 32)
+    enc = hd.hd_encode(codes, lengths, 128)
+    f = hd.DeviceField.upload(enc, lengths, n, device=f"cuda:{ctx_dev}")
+    out = torch.empty(n, dtype=torch.int16, device=f"cuda:{ctx_dev}")
+    ctx = hd.Context(ctx_dev)
+    best = ctx.autotune([f], [out], stream)
+
+    def timed():
+        ctx.decode(f, out, stream)
+        assert ctx.status(stream) == 0
+        assert np.array_equal(out.cpu().numpy().view(np.uint16), codes)
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.decode(f, out, stream)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    uniform = timed()
+    res = {"workload": f"{n} 1D codes in 32 segments at rel. error bounds 1e-2..1e-6 "
+                       f"({enc['nbits'] / n:.2f} bits/code overall), S=128 gap array",
+           "autotuned": best, "uniform_ms": uniform}
+    for classes in (4, 16):
+        ctx.set_config(subseq_bits=best["subseq_bits"], threads=best["threads"],
+                       lut_bits=best["lut_bits"], cr_classes=classes)
+        res[f"cr_classes_{classes}_ms"] = timed()
+    ctx.close()
+    res["note"] = ("class launches include the host read-back of the class sizes "
+                   "(a stream synchronisation) as Algorithm 2 does")
+    return res
+
+
 def run_batched(hd, torch, dev, stream, flush, fields_h, steps: int):
     """Config-3 leg: all fields in one graph launch (autotuned shape) against
     one hd_decode launch per field, same outputs."""
@@ -426,6 +476,7 @@ def run_gpu(args):
     lengths = hd.hd_build_codebook(codes, 1024, 32)
     enc = hd.hd_encode(codes, lengths, 128)
     fields_h = None
+    mixed_codes = mixed_cr_workload() if gen is not None else None
     if gen is not None:
         # the batched workload is encoded by the pool meanwhile; collect it
         # before anything is timed so that no host work overlaps a timing
@@ -535,6 +586,7 @@ def run_gpu(args):
 
     extra = {}
     if fields_h is not None:
+        extra["cr_class_ablation"] = run_cr_ablation(hd, torch, dev, stream, flush, mixed_codes)
         batched, dev_fields = run_batched(hd, torch, dev, stream, flush, fields_h, 3)
         extra["batched"] = batched
         extra["served"] = run_served(hd, dev, dev_fields, batched["ms_per_batch"],

@@ -131,6 +131,14 @@ typedef struct hd_config {
                            for alphabets up to 4096, whose tables have 16-bit
                            entries, else 12); a shape whose tables do not fit
                            shared memory fails with HD_ERR_ARG */
+  uint32_t cr_classes;  /* gap-array hd_decode only: 0 = one output window for
+                           all tiles; 2 .. 32 = per-tile compression-ratio
+                           classes (Sec. IV-C, Algorithm 2): after counting,
+                           tiles are sorted on the GPU into classes by their
+                           codeword count, the class sizes are read back, and
+                           one decode-and-write launch per class runs with a
+                           window sized for that class's largest tile (capped
+                           by shared memory) */
 } hd_config;
 
 /* Sets the launch shape used by later decodes on this context (NULL resets to

@@ -375,6 +375,55 @@ uint32_t kernels_per_launch(bool self_sync, bool sync_only) {
   return self_sync ? (sync_only ? 4u : 6u) : 4u;
 }
 
+// Gap-array decode with per-tile compression-ratio classes (Sec. IV-C,
+// Algorithm 2): count and scan as usual, sort the tiles into classes by
+// codeword count on the GPU, read the class sizes back (the paper also
+// returns its class histogram to the host), then one decode-and-write launch
+// per non-empty class with a window for that class: class c (compression
+// ratio in (c, c+1], i.e. up to (c+1) * B * S / 16 codewords per tile) gets
+// that many symbols, the last class the largest window shared memory holds.
+int queue_cr_classes(hd_ctx* c, hd::DecodeParams dp, const Prepared& P, char* cls,
+                     uint32_t nclass, cudaStream_t st) {
+  uint32_t* counts = reinterpret_cast<uint32_t*>(cls);
+  uint32_t* lists = reinterpret_cast<uint32_t*>(cls + 256);
+  const uint64_t cap = P.tiles;
+  const uint32_t unit = P.s.threads * P.s.S / 16;
+  if (hd::launch_phase(dp, P.s, hd::Phase::kCount, c->num_sms, st) != cudaSuccess ||
+      hd::launch_phase(dp, P.s, hd::Phase::kScan, c->num_sms, st) != cudaSuccess ||
+      cudaMemsetAsync(counts, 0, 4ull * nclass, st) != cudaSuccess ||
+      hd::launch_classify(dp, unit, nclass, counts, lists, cap, st) != cudaSuccess)
+    return HD_ERR_CUDA;
+  std::vector<uint32_t> n_in(nclass);
+  if (cudaMemcpyAsync(n_in.data(), counts, 4ull * nclass, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return HD_ERR_CUDA;
+  }
+  c->launches += 3;
+  const size_t budget = static_cast<size_t>(c->max_smem) - 2048;
+  for (uint32_t k = 0; k < nclass; ++k) {
+    if (!n_in[k]) continue;
+    hd::LaunchShape sh = P.s;
+    uint64_t want = static_cast<uint64_t>(k + 1) * unit;
+    if (k + 1 == nclass) want = 1ull << 20;
+    sh.window = static_cast<uint32_t>(align_up(std::max<uint64_t>(want, sh.S), 8));
+    sh.window = std::min<uint32_t>(sh.window, 1u << 20);
+    while (sh.window > std::max<uint32_t>(1024, sh.S) && hd::two_phase_smem_bytes(sh) > budget)
+      sh.window = sh.window > 4096 ? sh.window - 2048 : sh.window - 512;
+    if (hd::two_phase_smem_bytes(sh) > budget) return HD_ERR_ARG;
+    hd::DecodeParams d = dp;
+    d.window = sh.window;
+    d.tile_list = lists + k * cap;
+    d.unit_lo = 0;
+    d.unit_hi = n_in[k];
+    if (hd::launch_phase(d, sh, hd::Phase::kWrite, c->num_sms, st) != cudaSuccess)
+      return HD_ERR_CUDA;
+    c->launches += 1;
+  }
+  return HD_OK;
+}
+
 // Queues a decode of fields that all use the same strategy with direct
 // kernel launches (sizes as kernel parameters).
 int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape& shape,
@@ -385,7 +434,10 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
   if (rc) return rc;
   const Layout L = make_layout(nf, P.tiles, P.subs, P.tab_bytes, P.s, self_sync,
                                self_sync && !sync_only);
-  rc = ensure_ws(c, L.total);
+  const uint32_t nclass = self_sync ? 0u : c->cfg.cr_classes;
+  const size_t cls_off = L.total;  // CR classes: counts, then one tile list per class
+  const size_t cls_bytes = nclass ? 256 + 4ull * nclass * P.tiles : 0;
+  rc = ensure_ws(c, L.total + cls_bytes);
   if (rc) return rc;
   char* ws = c->ws;
   bind_descs(descs, ws, L, P, self_sync, sync_only);
@@ -407,6 +459,9 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
     if (self_sync) {
       e = hd::launch_sync(dp, P.s, c->num_sms, st);
       if (e == cudaSuccess && !sync_only) e = hd::launch_write(dp, P.s, c->num_sms, st);
+    } else if (nclass) {
+      rc = queue_cr_classes(c, dp, P, ws + cls_off, nclass, st);
+      if (rc) return rc;
     } else {
       e = hd::launch_decode_two_phase(dp, P.s, c->num_sms, st);
     }
@@ -556,7 +611,7 @@ hd::LaunchShape group_shape(const hd_ctx* c, const hd_field* fs, const std::vect
     syms += fs[i].n;
   }
   const hd_config& k = c->cfg;
-  const bool user = k.subseq_bits || k.threads || k.window || k.lut_bits;
+  const bool user = k.subseq_bits || k.threads || k.window || k.lut_bits || k.cr_classes;
   hd_config use = k;
   if (!user) {
     auto it = c->tuned.find(tune_key(gap, maxS, bits, syms));
@@ -866,6 +921,7 @@ int hd_set_config(hd_ctx* c, const hd_config* cfg) {
   if (cfg->threads && cfg->threads != 128 && cfg->threads != 256 && cfg->threads != 512)
     return HD_ERR_ARG;
   if (cfg->lut_bits && (cfg->lut_bits < 8 || cfg->lut_bits > 15)) return HD_ERR_ARG;
+  if (cfg->cr_classes && (cfg->cr_classes < 2 || cfg->cr_classes > 32)) return HD_ERR_ARG;
   if (cfg->window && (cfg->window < 64 || cfg->window > 32768)) return HD_ERR_ARG;
   c->cfg = *cfg;
   return HD_OK;
@@ -879,6 +935,7 @@ int hd_get_config(hd_ctx* c, hd_config* cfg) {
                  : c->last_shape.threads ? c->last_shape.threads : kDefaultThreads;
   cfg->window = c->cfg.window ? c->cfg.window : c->last_shape.window;
   cfg->lut_bits = c->cfg.lut_bits ? c->cfg.lut_bits : c->last_shape.K;
+  cfg->cr_classes = c->cfg.cr_classes;
   return HD_OK;
 }
 

@@ -119,6 +119,7 @@ struct DecodeParams {
   uint64_t unit_lo;         // two-phase kernels: process tiles [unit_lo, unit_hi) only
   uint64_t unit_hi;         // (0: up to total_units); k_scan continues from tile_base[unit_lo]
   uint64_t* scan_end;       // k_scan also stores tile_base[unit_hi] here (host-mapped; may be NULL)
+  const uint32_t* tile_list;  // k_write: tiles to process are tile_list[unit_lo .. unit_hi) (NULL: the range itself)
   uint64_t* unit_state;     // look-back state per tile (zeroed before launch)
   uint32_t* ticket;         // dynamic tile counter (zeroed before launch)
   uint32_t* abort_flag;     // set when any wait times out (zeroed before launch)

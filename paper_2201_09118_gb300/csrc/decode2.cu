@@ -192,24 +192,30 @@ __global__ void __launch_bounds__(B, write_min_blocks<B>())
   uint32_t* col = s_bits + t;
   uint32_t cur_field = 0xffffffffu;
   const LaunchSize LS = launch_size(P);
-  uint64_t g = LS.lo + blockIdx.x;
+  // the tiles come from a list when one is given (CR-class launches)
+  auto tile_of = [&](uint64_t v) -> uint64_t { return P.tile_list ? P.tile_list[v] : v; };
+  uint64_t u = LS.lo + blockIdx.x;
+  uint64_t g_next = 0;
   TileIn<S> nxt;
   uint32_t nfi = 0;
-  if (g < LS.units) {
-    nfi = find_field(P, LS, g);
-    fetch_tile<S, B, true>(nxt, P, field_of(P, LS, nfi), g);
+  if (u < LS.units) {
+    g_next = tile_of(u);
+    nfi = find_field(P, LS, g_next);
+    fetch_tile<S, B, true>(nxt, P, field_of(P, LS, nfi), g_next);
   }
-  for (; g < LS.units; g += gridDim.x) {
+  for (; u < LS.units; u += gridDim.x) {
+    const uint64_t g = g_next;
     const uint32_t fi = nfi;
     const FieldDesc& F = field_of(P, LS, fi);
     const uint64_t i = (g - F.unit_begin) * B + t;
     if (i < F.nsub) put_units<S>(col, nxt.bits, B);
     const uint32_t gap0 = nxt.gap0, count0 = nxt.count;
     if (t == 0) s_tile_base = nxt.base;
-    const uint64_t gn = g + gridDim.x;
-    if (gn < LS.units) {
-      nfi = find_field(P, LS, gn);
-      fetch_tile<S, B, true>(nxt, P, field_of(P, LS, nfi), gn);
+    const uint64_t un = u + gridDim.x;
+    if (un < LS.units) {
+      g_next = tile_of(un);
+      nfi = find_field(P, LS, g_next);
+      fetch_tile<S, B, true>(nxt, P, field_of(P, LS, nfi), g_next);
     }
     if (fi != cur_field) {
       __syncthreads();
@@ -250,6 +256,23 @@ __global__ void __launch_bounds__(B, write_min_blocks<B>())
                       }
                       if (bad) atomicOr(F.err, kErrCode);
                     });
+  }
+}
+
+// Shared-memory window classes (the per-sequence compression-ratio classes of
+// Algorithm 2, Sec. IV-C): tile g goes to class c when its codeword count is
+// in (c*unit, (c+1)*unit], the last class taking every larger tile; each
+// class keeps an unordered list of its tiles.
+__global__ void k_classify(const __grid_constant__ DecodeParams P, uint32_t unit, uint32_t nclass,
+                           uint32_t* counts, uint32_t* lists, uint64_t cap) {
+  const LaunchSize LS = launch_size(P);
+  for (uint64_t g = blockIdx.x * 256ull + threadIdx.x; g < LS.units;
+       g += static_cast<uint64_t>(gridDim.x) * 256) {
+    const uint32_t sym = P.tile_total[g];
+    uint32_t c = sym ? (sym - 1) / unit : 0u;
+    if (c >= nclass) c = nclass - 1;
+    const uint32_t slot = atomicAdd(counts + c, 1u);
+    lists[c * cap + slot] = static_cast<uint32_t>(g);
   }
 }
 
@@ -386,6 +409,16 @@ cudaError_t launch_phase(const DecodeParams& p, const LaunchShape& s, Phase phas
     case 512: return count ? launch_count_s<512>(p, s, num_sms, stream) : launch_write_only_s<512>(p, s, num_sms, stream);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_classify(const DecodeParams& p, uint32_t unit, uint32_t nclass,
+                            uint32_t* counts, uint32_t* lists, uint64_t cap, cudaStream_t stream) {
+  const uint64_t units = p.unit_hi ? p.unit_hi : p.total_units;
+  if (units == 0) return cudaSuccess;
+  const uint64_t blocks = (units + 255) / 256;
+  k_classify<<<static_cast<unsigned>(blocks < 4096 ? blocks : 4096), 256, 0, stream>>>(
+      p, unit, nclass, counts, lists, cap);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_write(const DecodeParams& p, const LaunchShape& s, int num_sms,

@@ -50,6 +50,13 @@ enum class Phase { kCount, kScan, kWrite };
 cudaError_t launch_phase(const DecodeParams& p, const LaunchShape& s, Phase phase, int num_sms,
                          cudaStream_t stream);
 
+// Sorts the tiles of a launch into nclass window classes by codeword count
+// (class c: counts in (c*unit, (c+1)*unit], the last class unbounded);
+// counts[c] (zeroed by the caller) receives the class sizes and
+// lists[c*cap ..] the tiles.  For CR-class decodes (Sec. IV-C, Algorithm 2).
+cudaError_t launch_classify(const DecodeParams& p, uint32_t unit, uint32_t nclass,
+                            uint32_t* counts, uint32_t* lists, uint64_t cap, cudaStream_t stream);
+
 // Tile scan and decode-and-write kernel, for fields whose counts and gap
 // entries are already in place (self-synchronisation writes them).
 cudaError_t launch_write(const DecodeParams& p, const LaunchShape& s, int num_sms,

@@ -54,7 +54,8 @@ class hd_field(ctypes.Structure):
 
 class hd_config(ctypes.Structure):
     _fields_ = [("subseq_bits", ctypes.c_uint32), ("threads", ctypes.c_uint32),
-                ("window", ctypes.c_uint32), ("lut_bits", ctypes.c_uint32)]
+                ("window", ctypes.c_uint32), ("lut_bits", ctypes.c_uint32),
+                ("cr_classes", ctypes.c_uint32)]
 
 
 class hd_serve_config(ctypes.Structure):
@@ -265,8 +266,8 @@ class Context:
         except Exception:
             pass
 
-    def set_config(self, subseq_bits=0, threads=0, window=0, lut_bits=0):
-        cfg = hd_config(subseq_bits, threads, window, lut_bits)
+    def set_config(self, subseq_bits=0, threads=0, window=0, lut_bits=0, cr_classes=0):
+        cfg = hd_config(subseq_bits, threads, window, lut_bits, cr_classes)
         _check("hd_set_config", self._lib.hd_set_config(self.handle, ctypes.byref(cfg)))
 
     def reset_config(self):
@@ -276,7 +277,7 @@ class Context:
         cfg = hd_config()
         _check("hd_get_config", self._lib.hd_get_config(self.handle, ctypes.byref(cfg)))
         return {"subseq_bits": cfg.subseq_bits, "threads": cfg.threads, "window": cfg.window,
-                "lut_bits": cfg.lut_bits}
+                "lut_bits": cfg.lut_bits, "cr_classes": cfg.cr_classes}
 
     def decode(self, field: DeviceField, out, stream=None) -> None:
         f = field.c_struct()
@@ -310,7 +311,7 @@ class Context:
         _check("hd_autotune", self._lib.hd_autotune(self.handle, arr, nf, ptrs,
                                                     _stream_handle(stream), ctypes.byref(cfg)))
         return {"subseq_bits": cfg.subseq_bits, "threads": cfg.threads, "window": cfg.window,
-                "lut_bits": cfg.lut_bits}
+                "lut_bits": cfg.lut_bits, "cr_classes": cfg.cr_classes}
 
     def graph_stats(self):
         cap = ctypes.c_uint64()

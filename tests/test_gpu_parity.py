@@ -103,6 +103,41 @@ def test_launch_shapes(ctx, S, threads, with_gap):
         ctx.reset_config()
 
 
+def mixed_cr_codes(n_seg=8, seg=1 << 18, seed=77):
+    """A field whose compressibility changes along it: segments quantized at
+    error bounds from 1e-2 (about 1 bit per code) to 1e-6 (about 8 bits)."""
+    parts = []
+    for k in range(n_seg):
+        eb = [1e-2, 1e-6, 1e-3, 1e-5, 1e-2, 1e-4, 1e-6, 1e-2][k % 8]
+        parts.append(synth.smooth_codes_1d(seg, eb, alphabet=1024, seed=seed + k))
+    return np.concatenate(parts)
+
+
+@pytest.mark.parametrize("classes", [2, 8, 32])
+@pytest.mark.parametrize("threads", [128, 512])
+def test_cr_class_launches(ctx, classes, threads):
+    # Algorithm 2 shaping: tiles sorted into window classes, one launch per class
+    x = mixed_cr_codes()
+    c = oracle.compress(x, 1024, S=128)
+    try:
+        ctx.set_config(threads=threads, cr_classes=classes)
+        check(ctx, c, True)
+        assert ctx.get_config()["cr_classes"] == classes
+        # corrupt count still detected, nothing written past n
+        cc = dict(c)
+        cc["n"] = c["n"] - 1
+        st, res = run_decode(ctx, cc, True)
+        assert st == hd_codes().HD_ERR_CORRUPT
+        assert np.all(res[cc["n"]:] == np.uint16(CANARY))
+    finally:
+        ctx.reset_config()
+
+
+def hd_codes():
+    from paper_2201_09118_gb300 import hd
+    return hd
+
+
 @pytest.mark.parametrize("dec_S", [128, 256, 512])
 def test_decoder_subsequence_multiple_of_stream(ctx, dec_S):
     x = synth.laplace_codes(100000, scale=3.0, seed=5)
