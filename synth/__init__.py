@@ -15,11 +15,14 @@ in for them:
 * ``fourier_field``      smooth float32 fields (1D/2D/3D) made of random
                          Fourier modes with 1/|k|^2 amplitudes plus Gaussian
                          noise.
-* ``lorenzo_codes``      cuSZ-style error-bounded quantization followed by the
+* ``lorenzo_quantize``   cuSZ-style error-bounded quantization followed by the
                          integer first-order Lorenzo predictor, giving the
-                         residue codes the decoder consumes.  The paper does
-                         not describe this step (it only cites cuSZ); it is a
+                         residue codes the decoder consumes and the outliers
+                         (residues beyond the radius) kept aside for the
+                         reconstruction after it.  The paper does not
+                         describe this step (it only cites cuSZ); it is a
                          test-input generator here and is never timed.
+* ``lorenzo_codes``      the codes alone.
 * ``batch_spec``         the size / alphabet / error-bound mix of a batch of
                          independent fields.
 
@@ -35,9 +38,11 @@ import numpy as np
 __all__ = [
     "laplace_codes",
     "fourier_field",
+    "lorenzo_quantize",
     "lorenzo_codes",
     "smooth_codes_1d",
     "field3d_codes",
+    "field3d_quantized",
     "batch_spec",
     "FieldSpec",
     "code_stats",
@@ -127,12 +132,16 @@ def fourier_field(shape, n_modes: int = 64, noise: float = 0.01, kmax: int = 8,
     return smooth
 
 
-def lorenzo_codes(field: np.ndarray, rel_eb: float, radius: int = 512):
-    """cuSZ-style codes: q = round(x / 2eb) (half away from zero), integer
-    first-order Lorenzo residue d (zero outside the domain), code = d + radius
-    when |d| < radius else 0 (an outlier, kept aside by the compressor).
+def lorenzo_quantize(field: np.ndarray, rel_eb: float, radius: int = 512,
+                     keep_q: bool = False) -> dict:
+    """cuSZ-style codes with their outliers: q = round(x / 2eb) (half away
+    from zero), integer first-order Lorenzo residue d (zero outside the
+    domain), code = d + radius when |d| < radius, else 0 with d kept aside.
 
-    Returns ``(codes uint16, eb, outlier_fraction)``.
+    Returns a dict: ``codes`` (uint16, flat, x fastest), ``eb``,
+    ``out_idx`` (uint64, ascending flat positions of code 0), ``out_val``
+    (int32 residues there), ``out_frac`` and, with ``keep_q``, ``q`` (int64,
+    the prequantized values, shaped like the field).
     """
     field = np.asarray(field)
     lo = float(field.min())
@@ -141,7 +150,7 @@ def lorenzo_codes(field: np.ndarray, rel_eb: float, radius: int = 512):
     scaled = field.astype(np.float64) / (2.0 * eb)
     q = (np.sign(scaled) * np.floor(np.abs(scaled) + 0.5)).astype(np.int64)
     del scaled
-    d = q
+    d = q.copy() if keep_q else q
     # (1 - S_x)(1 - S_y)(1 - S_z) q: the 1D/2D/3D Lorenzo residue
     for ax in range(d.ndim):
         sl_hi = [slice(None)] * d.ndim
@@ -149,10 +158,29 @@ def lorenzo_codes(field: np.ndarray, rel_eb: float, radius: int = 512):
         sl_hi[ax] = slice(1, None)
         sl_lo[ax] = slice(None, -1)
         d[tuple(sl_hi)] -= d[tuple(sl_lo)].copy()
+    d = d.reshape(-1)
     inlier = np.abs(d) < radius
     codes = np.where(inlier, d + radius, 0).astype(np.uint16)
-    out_frac = 1.0 - float(np.count_nonzero(inlier)) / max(1, d.size)
-    return codes.reshape(-1), eb, out_frac
+    out_idx = np.flatnonzero(~inlier).astype(np.uint64)
+    out_val = d[out_idx.astype(np.int64)]
+    if out_val.size and (out_val.min() < -(1 << 31) or out_val.max() >= (1 << 31)):
+        raise ValueError("outlier residue outside int32")
+    res = {
+        "codes": codes,
+        "eb": eb,
+        "out_idx": out_idx,
+        "out_val": out_val.astype(np.int32),
+        "out_frac": float(out_idx.size) / max(1, d.size),
+    }
+    if keep_q:
+        res["q"] = q
+    return res
+
+
+def lorenzo_codes(field: np.ndarray, rel_eb: float, radius: int = 512):
+    """The codes of ``lorenzo_quantize``: ``(codes uint16, eb, outlier_fraction)``."""
+    r = lorenzo_quantize(field, rel_eb, radius)
+    return r["codes"], r["eb"], r["out_frac"]
 
 
 def smooth_codes_1d(n: int, rel_eb: float, alphabet: int = 1024, noise: float = 1e-4,
@@ -166,9 +194,18 @@ def smooth_codes_1d(n: int, rel_eb: float, alphabet: int = 1024, noise: float = 
 def field3d_codes(side: int = 512, rel_eb: float = 1e-4, noise: float = 0.01,
                   seed: int = 1001) -> np.ndarray:
     """The 3D workload: side^3 smooth field + noise, 3D Lorenzo, radius 512."""
+    return field3d_quantized(side, rel_eb, noise, seed)["codes"]
+
+
+def field3d_quantized(side: int = 512, rel_eb: float = 1e-4, noise: float = 0.01,
+                      seed: int = 1001, keep_field: bool = False) -> dict:
+    """``lorenzo_quantize`` of the 3D workload (codes, eb, outliers); with
+    ``keep_field`` also the float32 field itself under ``field``."""
     f = fourier_field((side, side, side), noise=noise, kmax=8, seed=seed)
-    codes, _, _ = lorenzo_codes(f, rel_eb, radius=512)
-    return codes
+    r = lorenzo_quantize(f, rel_eb, radius=512)
+    if keep_field:
+        r["field"] = f
+    return r
 
 
 @dataclass
