@@ -73,9 +73,14 @@ def whole_job_gbps(codes_per_rank: int, steps: int, world: int, max_ms: float) -
     return 2.0 * codes_per_rank * steps * world / (max_ms * 1e-3) / 1e9
 
 
-def workload_codes(side: int, seed: int):
+def workload_quantized(side: int, seed: int, keep_field: bool = False):
     import synth
-    return synth.field3d_codes(side, rel_eb=1e-4, noise=0.01, seed=seed)
+    return synth.field3d_quantized(side, rel_eb=1e-4, noise=0.01, seed=seed,
+                                   keep_field=keep_field)
+
+
+def workload_codes(side: int, seed: int):
+    return workload_quantized(side, seed)["codes"]
 
 
 def workload_desc(side: int) -> str:
@@ -287,6 +292,63 @@ def run_encode(hd, torch, ctx, codes, lengths, enc, stream, flush, steps: int = 
             "timing": "wall clock around the synchronous call (incl. its length read-back)"}
 
 
+def run_decompress(hd, torch, ctx, field, dec_codes, g, stream, flush, steps: int = 5):
+    """The step after the decoder: Lorenzo reconstruction of the decoded codes
+    into float32 (hd_reconstruct_device), and decode + reconstruction in one
+    call (hd_decompress_device), on the same field; values checked against the
+    original field's error bound."""
+    side = round(dec_codes.numel() ** (1 / 3))
+    dims = (side, side, side)
+    dev = dec_codes.device
+    idx = torch.from_numpy(g["out_idx"].view(np.int64)).to(dev)
+    val = torch.from_numpy(g["out_val"]).to(dev)
+    n = dec_codes.numel()
+    fout = torch.empty(n, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        fn()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    L = hd.lorenzo_params(dims, 512, g["eb"], idx, val)
+    recon_ms = timed(lambda: ctx.reconstruct(dec_codes, L, fout, stream))
+    ok = ctx.status(stream) == 0
+    sweep = {}
+    for zc in (1, 8, 16, 64, side):
+        Lz = hd.lorenzo_params(dims, 512, g["eb"], idx, val, zc)
+        sweep[str(zc)] = timed(lambda: ctx.reconstruct(dec_codes, Lz, fout, stream))
+    dec_ms = timed(lambda: ctx.decompress(field, L, fout, stream))
+    ok = ok and ctx.status(stream) == 0
+    f = g.get("field")
+    bound_ok = None
+    if f is not None:
+        x = fout.cpu().numpy().astype(np.float64)
+        fl = f.reshape(-1).astype(np.float64)
+        bound_ok = bool(np.all(np.abs(x - fl) <= g["eb"] * (1 + 1e-6) + 2.0 ** -23 * np.abs(fl)))
+    alg = 2 * n + 4 * n + 12 * int(g["out_idx"].size)
+    peak, kind = measured_peak()
+    return {"workload": f"{side}^3 codes of the decode workload -> float32, "
+                        f"{g['out_idx'].size} outliers, abs. error bound {g['eb']:.6g}",
+            "value": 4.0 * n / (dec_ms * 1e-3) / 1e9,
+            "unit": "GB/s (float32 values out, decode + reconstruction)",
+            "decompress_ms": dec_ms, "reconstruct_ms": recon_ms,
+            "reconstruct_slice_groups_ms": sweep,
+            "reconstruct_roofline": {"bound": "hbm", "achieved": alg / (recon_ms * 1e-3) / 1e9,
+                                     "peak": peak, "unit": "GB/s",
+                                     "frac": alg / (recon_ms * 1e-3) / 1e9 / peak,
+                                     "peak_kind": kind, "algorithmic_bytes": alg},
+            "status_ok": bool(ok), "within_error_bound": bound_ok}
+
+
 def mixed_cr_workload(n_seg: int = 32, seg: int = 1 << 21, seed: int = 1005):
     """A 1D field whose compressibility changes along it (segments quantized at
     error bounds 1e-2 .. 1e-6), for the window-class ablation."""
@@ -471,7 +533,8 @@ def run_gpu(args):
     dev = torch.cuda.current_device()
 
     side = args.side
-    codes = workload_codes(side, seed=1001 + rank)
+    quant = workload_quantized(side, seed=1001 + rank, keep_field=rank == 0)
+    codes = quant["codes"]
     n = codes.size
     lengths = hd.hd_build_codebook(codes, 1024, 32)
     enc = hd.hd_encode(codes, lengths, 128)
@@ -585,6 +648,8 @@ def run_gpu(args):
         return 0
 
     extra = {}
+    extra["decompress"] = run_decompress(hd, torch, ctx, field, out, quant, stream, flush)
+    quant.pop("field", None)
     if fields_h is not None:
         extra["cr_class_ablation"] = run_cr_ablation(hd, torch, dev, stream, flush, mixed_codes)
         batched, dev_fields = run_batched(hd, torch, dev, stream, flush, fields_h, 3)

@@ -312,6 +312,54 @@ int hd_serve_completed(hd_server* srv, uint64_t* tickets, uint32_t cap, uint32_t
 int hd_serve_drain(hd_server* srv);
 int hd_serve_stats(hd_server* srv, hd_serve_stats_t* out);
 
+/* ---- Reconstruction (the step after the decoder) ------------------------ */
+
+/* cuSZ's Lorenzo reconstruction, the second half of the end-to-end
+ * decompression the paper measures (Sec. V-B2; the paper cites cuSZ for it
+ * and does not define it).  Reading: first-order Lorenzo prediction on
+ * prequantized integers, zero outside the domain.  A code c in [1, 2R)
+ * stands for the residue d = c - R; code 0 marks an outlier whose residue is
+ * stored aside.  The prequantized value q is the inclusive prefix sum of d
+ * along every axis, and the output value is float32(q) * float32(2 eb) (each
+ * conversion rounded to nearest even).  q must stay within int32. */
+typedef struct hd_lorenzo {
+  uint32_t ndim;           /* 1, 2 or 3 */
+  uint32_t radius;         /* R, 1 .. 32768 */
+  uint64_t dims[3];        /* extents, dims[0] varying fastest; entries >= ndim ignored.
+                              2D/3D: dims[0] <= 49152 */
+  double eb;               /* absolute error bound (finite, >= 0) */
+  const uint64_t* out_idx; /* device: ascending positions whose code is 0 [n_out] */
+  const int32_t* out_val;  /* device: their residues [n_out] */
+  uint64_t n_out;
+  uint32_t chunk_slices;   /* band path, 3D: slices reconstructed per group, whose
+                              int32 intermediate may stay in L2 (0 = about 32 MB
+                              of it) */
+  uint32_t band_rows;      /* band path: rows per band, 1 .. 64 (0 = 8 for rows
+                              up to 1024 codes, else as many as 64 KB of shared
+                              memory holds, at most 32) */
+} hd_lorenzo;
+
+/* Reconstructs dims[0]*..*dims[ndim-1] float32 values into d_out (device,
+ * 16-byte aligned) from the codes d_codes (device, 16-byte aligned).  1D:
+ * one kernel (a decoupled look-back scan over tiles of 8192 codes).  3D with
+ * rows up to 1024 codes and at least two slices per SM (and chunk_slices =
+ * band_rows = 0): the slice path, one block per slice for the x and y
+ * prefixes (int32 written into d_out), then a z kernel that writes the floats
+ * in place.  Otherwise the band path: per group of slices a band kernel (a
+ * warp per band of rows in registers, or a block per band in shared memory
+ * for longer rows), a band-carry scan and the z kernel with the carries.  Queued on `stream`; hd_status reports HD_ERR_CORRUPT for
+ * a code 0 the outlier list lacks (its residue is taken as 0) and
+ * HD_ERR_TIMEOUT for a look-back wait that gave up.  HD_ERR_ARG for invalid
+ * parameters or alignment. */
+int hd_reconstruct_device(hd_ctx* ctx, const uint16_t* d_codes, const hd_lorenzo* L,
+                          float* d_out, void* stream);
+
+/* Decompression: hd_decode of f (device field, f->n = the grid size) into a
+ * context-owned code buffer, then hd_reconstruct_device into d_out.  One
+ * status for both through hd_status. */
+int hd_decompress_device(hd_ctx* ctx, const hd_field* f, const hd_lorenzo* L, float* d_out,
+                         void* stream);
+
 /* ---- GPU encoding (the step before the decoder) ------------------------- */
 
 /* Symbol counts of d_codes[0 .. n) (device) into freq_out[alphabet] (host).

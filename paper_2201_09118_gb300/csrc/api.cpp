@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -61,6 +62,14 @@ struct hd_ctx {
   uint64_t* pin_ends_dev = nullptr;  // the same memory as the device sees it
   // autotuner results: batch class -> launch shape
   std::map<TuneKey, hd_config> tuned;
+  // Lorenzo reconstruction: its workspace (error word first), whether its
+  // error word belongs to the last queued operation, decoded codes of
+  // hd_decompress_device
+  char* rws = nullptr;
+  size_t rws_cap = 0;
+  bool recon_active = false;
+  uint16_t* dcodes = nullptr;
+  size_t dcodes_cap = 0;
 };
 
 namespace {
@@ -471,6 +480,7 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
   c->launches += kernels_per_launch(self_sync, sync_only);
   c->err_off = L.err;
   c->err_count = nf;
+  c->recon_active = false;
   c->last_shape = P.s;
   return HD_OK;
 }
@@ -570,6 +580,7 @@ int queue_decode_graph(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::Launc
   c->launches += kernels_per_launch(self_sync, false);
   c->err_off = L.err;
   c->err_count = nf;
+  c->recon_active = false;
   c->last_shape = P.s;
   return HD_OK;
 }
@@ -657,6 +668,7 @@ int plan_batch(hd_ctx* c, const hd_field* fs, uint32_t nf, uint16_t* const* d_ou
 int decode_batch_locked(hd_ctx* c, const hd_field* fs, uint32_t nf, uint16_t* const* d_outs,
                         void* stream) {
   c->err_count = 0;
+  c->recon_active = false;
   c->host_status = HD_OK;
   c->err_map.assign(nf, 0xffffffffu);
   if (nf == 0) return HD_OK;
@@ -709,6 +721,7 @@ int decode_batch_locked(hd_ctx* c, const hd_field* fs, uint32_t nf, uint16_t* co
   }
   // both groups ran: the per-field results are kept on the host
   c->err_count = 0;
+  c->recon_active = false;
   for (uint32_t i = 0; i < nf; ++i) c->err_map[i] = 0x80000000u | merged[i];
   return HD_OK;
 }
@@ -849,6 +862,7 @@ int decode_host_pipelined(hd_ctx* c, const hd_field* f, uint16_t* host_out, cuda
     return HD_ERR_CUDA;
   c->err_off = L.err;
   c->err_count = 1;
+  c->recon_active = false;
   c->host_status = HD_OK;
   c->last_shape = P.s;
   return HD_OK;
@@ -904,6 +918,8 @@ int hd_ctx_destroy(hd_ctx* c) {
       if (e) cudaEventDestroy(e);
     if (c->ws) cudaFree(c->ws);
     if (c->stage) cudaFree(c->stage);
+    if (c->rws) cudaFree(c->rws);
+    if (c->dcodes) cudaFree(c->dcodes);
     for (auto e : c->events) cudaEventDestroy(e);
   }
   delete c;
@@ -944,6 +960,7 @@ static int decode_impl(hd_ctx* c, const hd_field* f, uint16_t* d_out, uint8_t* g
   const bool sync_only = gap_out != nullptr;
   int rc = check_field(f, !sync_only, d_out);
   c->err_count = 0;
+  c->recon_active = false;
   if (rc == HD_PENDING) {
     c->host_status = HD_OK;
     return HD_OK;
@@ -1002,6 +1019,14 @@ int hd_status(hd_ctx* c, void* stream) {
   if (c->host_status != HD_OK) return c->host_status;
   uint32_t all = 0;
   for (uint32_t b : bits) all |= b;
+  if (c->recon_active) {
+    uint32_t r = 0;
+    if (cudaMemcpy(&r, c->rws, 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return HD_ERR_CUDA;
+    }
+    all |= r;
+  }
   return map_err_bits(all);
 }
 
@@ -1099,6 +1124,7 @@ int hd_autotune(hd_ctx* c, const hd_field* fs, uint32_t nf, uint16_t* const* d_o
   c->profile = saved_profile;
   drop_graphs(c);  // keep only what later batches use (recaptured on demand)
   c->err_count = 0;
+  c->recon_active = false;
   c->err_map.clear();
   return rc;
 }
@@ -1204,6 +1230,7 @@ int hd_histogram_device(hd_ctx* c, const uint16_t* d_codes, uint64_t n, uint32_t
   }
   c->launches += n ? 1 : 0;
   c->err_count = 0;
+  c->recon_active = false;
   return err ? HD_ERR_SYMBOL : HD_OK;
 }
 
@@ -1232,6 +1259,7 @@ int hd_encode_device(hd_ctx* c, const uint16_t* d_codes, uint64_t n, const uint8
   if (rc) return rc;
   char* ws = c->ws;
   c->err_count = 0;  // hd_status does not report encodes
+  c->recon_active = false;
   hd::EncodeParams e{};
   e.codes = d_codes;
   e.n = n;
@@ -1280,6 +1308,181 @@ int hd_encode_device(hd_ctx* c, const uint16_t* d_codes, uint64_t n, const uint8
     return HD_ERR_CUDA;
   }
   return HD_OK;
+}
+
+// ---- Lorenzo reconstruction -------------------------------------------------
+
+static constexpr uint64_t kReconMaxRow = 49152;          // 2D/3D row limit (band shared memory)
+static constexpr uint64_t kReconGroupBytes = 32ull << 20;  // int32 intermediate per slice group
+
+static int reconstruct_locked(hd_ctx* c, const uint16_t* d_codes, const hd_lorenzo* L,
+                              float* d_out, void* stream) {
+  c->err_count = 0;
+  c->recon_active = false;
+  c->host_status = HD_ERR_ARG;
+  if (!L || L->ndim < 1 || L->ndim > 3) return HD_ERR_ARG;
+  if (L->radius < 1 || L->radius > 32768) return HD_ERR_ARG;
+  if (!(L->eb >= 0.0) || !std::isfinite(L->eb)) return HD_ERR_ARG;
+  const float ebx2 = static_cast<float>(2.0 * L->eb);
+  if (!std::isfinite(ebx2)) return HD_ERR_ARG;
+  uint64_t ext[3] = {1, 1, 1};
+  uint64_t n = 1;
+  for (uint32_t k = 0; k < L->ndim; ++k) {
+    ext[k] = L->dims[k];
+    if (ext[k] && n > (1ull << 48) / ext[k]) return HD_ERR_ARG;
+    n *= ext[k];
+  }
+  if (L->n_out > n || (L->n_out && (!L->out_idx || !L->out_val))) return HD_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(L->out_idx) & 7u) || (reinterpret_cast<uintptr_t>(L->out_val) & 3u))
+    return HD_ERR_ARG;
+  if (n && (!d_codes || !d_out)) return HD_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_codes) & 15u) || (reinterpret_cast<uintptr_t>(d_out) & 15u))
+    return HD_ERR_ARG;
+  const bool one_d = L->ndim == 1;
+  if (!one_d && ext[0] > kReconMaxRow) return HD_ERR_ARG;
+  if (one_d && hd::lorenzo_tiles_1d(n) > 0x7fffffffull) return HD_ERR_ARG;
+  if (!one_d && L->band_rows > 64) return HD_ERR_ARG;
+  if (!n) {
+    c->host_status = HD_OK;
+    return HD_OK;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  hd::LorenzoParams P{};
+  P.codes = d_codes;
+  P.out = d_out;
+  P.n = n;
+  P.radius = static_cast<int32_t>(L->radius);
+  P.ebx2 = ebx2;
+  P.out_idx = L->out_idx;
+  P.out_val = L->out_val;
+  P.n_out = L->n_out;
+  P.timeout_cycles = 4000000000ull;  // about 2 s at the SM clock
+  size_t need = 256;
+  uint64_t zc = 1;
+  // 3D grids with many slices and rows up to 1024 codes: one block per
+  // slice, then the z kernel (no band carries); a launch shape given for the
+  // band path selects that instead
+  const bool slice_path = L->ndim == 3 && !L->chunk_slices && !L->band_rows &&
+                          hd::lorenzo_slice_path(ext[0], ext[2], c->num_sms);
+  if (one_d) {
+    P.nx = n;
+    P.ny = P.nz = 1;
+    need += 8ull * hd::lorenzo_tiles_1d(n);
+  } else if (slice_path) {
+    P.nx = ext[0];
+    P.ny = ext[1];
+    P.nz = ext[2];
+  } else {
+    P.nx = ext[0];
+    P.ny = ext[1];
+    P.nz = L->ndim == 3 ? ext[2] : 1;
+    P.yb = L->band_rows ? L->band_rows : hd::lorenzo_rows_per_band(P.nx);
+    P.nb = (P.ny + P.yb - 1) / P.yb;
+    const uint64_t plane_bytes = 4ull * P.ny * P.nx;
+    zc = L->chunk_slices ? L->chunk_slices
+                         : std::max<uint64_t>(1, kReconGroupBytes / plane_bytes);
+    zc = std::min<uint64_t>(zc, P.nz);
+    if (hd::lorenzo_band_smem(P.yb, P.nx) > static_cast<size_t>(c->max_smem)) return HD_ERR_ARG;
+    if (zc * P.nb > 0x7fffffffull) zc = std::max<uint64_t>(1, 0x7fffffffull / P.nb);
+    need = align_up(need, 256) + align_up(4ull * zc * P.nb * P.nx, 256) + plane_bytes;
+  }
+  c->host_status = HD_OK;
+  if (need > c->rws_cap) {
+    if (c->rws) {
+      cudaDeviceSynchronize();
+      cudaFree(c->rws);
+      c->rws = nullptr;
+      c->rws_cap = 0;
+    }
+    const size_t cap = align_up(std::max<size_t>(need, 1 << 20), 1 << 20);
+    if (cudaMalloc(&c->rws, cap) != cudaSuccess) {
+      cudaGetLastError();
+      c->host_status = HD_ERR_NOMEM;
+      return HD_ERR_NOMEM;
+    }
+    c->rws_cap = cap;
+  }
+  P.err = reinterpret_cast<uint32_t*>(c->rws);
+  P.ticket = reinterpret_cast<uint32_t*>(c->rws + 128);
+  P.state = reinterpret_cast<unsigned long long*>(c->rws + 256);
+  P.band = reinterpret_cast<int32_t*>(c->rws + 256);
+  P.plane = reinterpret_cast<int32_t*>(c->rws + 256 + align_up(4ull * zc * P.nb * P.nx, 256));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->profile) {
+    e0 = next_event(c);
+    e1 = next_event(c);
+  }
+  cudaError_t e = cudaMemsetAsync(c->rws, 0, 4, st);
+  if (e == cudaSuccess && c->profile) e = cudaEventRecord(e0, st);
+  uint64_t launches = 0;
+  if (one_d) {
+    if (e == cudaSuccess) e = hd::launch_lorenzo_1d(P, st);
+    launches = 1;
+  } else if (slice_path) {
+    P.z_lo = 0;
+    P.z_hi = P.nz;
+    if (e == cudaSuccess) e = hd::launch_lorenzo_whole_slices(P, c->num_sms, st);
+    launches = 2;
+  } else {
+    for (uint64_t z = 0; z < P.nz && e == cudaSuccess; z += zc) {
+      P.z_lo = z;
+      P.z_hi = std::min(P.nz, z + zc);
+      e = hd::launch_lorenzo_slices(P, c->num_sms, st);
+      launches += 3;
+    }
+  }
+  if (e == cudaSuccess && c->profile) e = cudaEventRecord(e1, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->host_status = HD_ERR_CUDA;
+    return HD_ERR_CUDA;
+  }
+  c->launches += launches;
+  c->recon_active = true;
+  return HD_OK;
+}
+
+int hd_reconstruct_device(hd_ctx* c, const uint16_t* d_codes, const hd_lorenzo* L, float* d_out,
+                          void* stream) {
+  if (!c) return HD_ERR_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  return reconstruct_locked(c, d_codes, L, d_out, stream);
+}
+
+int hd_decompress_device(hd_ctx* c, const hd_field* f, const hd_lorenzo* L, float* d_out,
+                         void* stream) {
+  if (!c || !f || !L) return HD_ERR_ARG;
+  uint64_t n = 1;
+  for (uint32_t k = 0; k < L->ndim && k < 3; ++k) n *= L->dims[k];
+  if (L->ndim < 1 || L->ndim > 3 || f->n != n) return HD_ERR_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  const size_t bytes = align_up(2 * n + 16, 256);
+  if (bytes > c->dcodes_cap) {
+    if (c->dcodes) {
+      cudaDeviceSynchronize();
+      cudaFree(c->dcodes);
+      c->dcodes = nullptr;
+      c->dcodes_cap = 0;
+    }
+    if (cudaMalloc(&c->dcodes, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return HD_ERR_NOMEM;
+    }
+    c->dcodes_cap = bytes;
+  }
+  int rc = decode_impl(c, f, c->dcodes, nullptr, stream);
+  if (rc) return rc;
+  if (c->host_status != HD_OK) return HD_OK;  // hd_status reports it; nothing to reconstruct
+  const uint32_t err_words = c->err_count;
+  const size_t err_off = c->err_off;
+  rc = reconstruct_locked(c, c->dcodes, L, d_out, stream);
+  // hd_status reports the decode's error words and the reconstruction's
+  c->err_count = err_words;
+  c->err_off = err_off;
+  return rc;
 }
 
 int hd_profile(hd_ctx* c, int enable) {

@@ -94,6 +94,7 @@ enum : uint32_t {
   kErrTimeout = 8u,  // a look-back wait gave up
   kErrNoSync = 16u,  // self-synchronisation hit its round cap
   kErrTable = 32u,   // invalid code-length table
+  kErrOutlier = 64u, // reconstruction: code 0 at a position the outlier list lacks
 };
 
 // Sizes of a launch kept in device memory.  Graph launches read their field
@@ -161,6 +162,31 @@ struct EncodeParams {
   uint8_t* gap;               // gap array [nsub] or NULL
   uint64_t nsub;
   uint32_t* err;              // bit 0: a symbol without a code
+};
+
+// Lorenzo reconstruction (lorenzo.cu): codes -> residues -> prefix sums
+// along every axis -> float32 values 2 eb q.
+struct LorenzoParams {
+  const uint16_t* codes;     // quantization codes [n], x fastest (16-byte aligned)
+  float* out;                // values [n] (16-byte aligned); 2D/3D: also the int32 intermediate
+  uint64_t n;
+  uint64_t nx, ny, nz;       // extents (1D: nx = n, ny = nz = 1)
+  int32_t radius;            // residue = code - radius; code 0 = outlier
+  float ebx2;                // float32(2 eb)
+  const uint64_t* out_idx;   // outlier positions, ascending [n_out]
+  const int32_t* out_val;    // outlier residues [n_out]
+  uint64_t n_out;
+  uint32_t* err;             // error bits
+  // 2D/3D: bands of yb rows within a slice; launches cover slices [z_lo, z_hi)
+  uint32_t yb;
+  uint64_t nb;               // bands per slice
+  int32_t* band;             // per (slice of the launch, band, x): band column totals
+  int32_t* plane;            // running z-sum of every (y, x) between launches [ny * nx]
+  uint64_t z_lo, z_hi;
+  // 1D: decoupled look-back over tiles
+  unsigned long long* state; // per tile (zeroed before the launch)
+  uint32_t* ticket;          // tile counter (zeroed before the launch)
+  uint64_t timeout_cycles;
 };
 
 // Look-back state word: flag in bits 62..63, value in bits 0..61.

@@ -75,6 +75,32 @@ class hd_serve_stats_t(ctypes.Structure):
                                                 "peak_bytes")]
 
 
+class hd_lorenzo(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_uint32), ("radius", ctypes.c_uint32),
+                ("dims", ctypes.c_uint64 * 3), ("eb", ctypes.c_double),
+                ("out_idx", ctypes.c_void_p), ("out_val", ctypes.c_void_p),
+                ("n_out", ctypes.c_uint64), ("chunk_slices", ctypes.c_uint32),
+                ("band_rows", ctypes.c_uint32)]
+
+
+def lorenzo_params(dims, radius: int, eb: float, out_idx=None, out_val=None,
+                   chunk_slices: int = 0, band_rows: int = 0) -> hd_lorenzo:
+    """hd_lorenzo for a grid (dims[0] fastest) and device outlier tensors."""
+    L = hd_lorenzo()
+    L.ndim = len(dims)
+    for k, v in enumerate(dims):
+        L.dims[k] = int(v)
+    L.radius = int(radius)
+    L.eb = float(eb)
+    n_out = 0 if out_idx is None else int(out_idx.numel())
+    L.out_idx = out_idx.data_ptr() if n_out else None
+    L.out_val = out_val.data_ptr() if n_out else None
+    L.n_out = n_out
+    L.chunk_slices = int(chunk_slices)
+    L.band_rows = int(band_rows)
+    return L
+
+
 # every exported symbol of include/hd.h with its ctypes signature
 _P = ctypes.c_void_p
 _SIGS = {
@@ -88,6 +114,9 @@ _SIGS = {
     "hd_encode_device": ([_P, _P, ctypes.c_uint64, _P, ctypes.c_uint32, ctypes.c_uint32, _P,
                           ctypes.c_uint64, _P, ctypes.c_uint64, ctypes.POINTER(hd_stream_info),
                           _P], ctypes.c_int),
+    "hd_reconstruct_device": ([_P, _P, ctypes.POINTER(hd_lorenzo), _P, _P], ctypes.c_int),
+    "hd_decompress_device": ([_P, ctypes.POINTER(hd_field), ctypes.POINTER(hd_lorenzo), _P, _P],
+                             ctypes.c_int),
     "hd_ctx_create": ([ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
     "hd_ctx_destroy": ([_P], ctypes.c_int),
     "hd_set_config": ([_P, ctypes.POINTER(hd_config)], ctypes.c_int),
@@ -287,6 +316,20 @@ class Context:
 
     def status(self, stream=None) -> int:
         return self._lib.hd_status(self.handle, _stream_handle(stream))
+
+    def reconstruct(self, codes, L: hd_lorenzo, out, stream=None) -> None:
+        """Lorenzo reconstruction of device codes (uint16 as int16) into a
+        float32 device tensor (hd_reconstruct_device)."""
+        _check("hd_reconstruct_device", self._lib.hd_reconstruct_device(
+            self.handle, ctypes.c_void_p(codes.data_ptr()), ctypes.byref(L),
+            ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+
+    def decompress(self, field: DeviceField, L: hd_lorenzo, out, stream=None) -> None:
+        """Decode then reconstruct (hd_decompress_device)."""
+        f = field.c_struct()
+        _check("hd_decompress_device", self._lib.hd_decompress_device(
+            self.handle, ctypes.byref(f), ctypes.byref(L), ctypes.c_void_p(out.data_ptr()),
+            _stream_handle(stream)))
 
     def sync_points(self, field: DeviceField, gap_out, stream=None) -> None:
         f = field.c_struct()
