@@ -340,16 +340,18 @@ typedef struct hd_lorenzo {
 } hd_lorenzo;
 
 /* Reconstructs dims[0]*..*dims[ndim-1] float32 values into d_out (device,
- * 16-byte aligned) from the codes d_codes (device, 16-byte aligned).  1D:
- * one kernel (a decoupled look-back scan over tiles of 8192 codes).  3D with
- * rows up to 1024 codes and at least two slices per SM (and chunk_slices =
- * band_rows = 0): the slice path, one block per slice for the x and y
- * prefixes (int32 written into d_out), then a z kernel that writes the floats
- * in place.  Otherwise the band path: per group of slices a band kernel (a
- * warp per band of rows in registers, or a block per band in shared memory
- * for longer rows), a band-carry scan and the z kernel with the carries.  Queued on `stream`; hd_status reports HD_ERR_CORRUPT for
- * a code 0 the outlier list lacks (its residue is taken as 0) and
- * HD_ERR_TIMEOUT for a look-back wait that gave up.  HD_ERR_ARG for invalid
+ * 16-byte aligned) from the codes d_codes (device, 16-byte aligned).
+ * 1D: residue sums of tiles of 8192 codes, their scan, and a pass that
+ * rescans each tile from its prefix.
+ * 3D with rows up to 1024 codes and at least two slices per SM (and
+ * chunk_slices = band_rows = 0), the slice path: one block per slice for the
+ * x and y prefixes (int32 written into d_out), then a z kernel that writes
+ * the floats in place.
+ * Otherwise the band path: per group of slices a band kernel (a warp per
+ * band of rows in registers, or a block per band in shared memory for longer
+ * rows), a band-carry scan and the z kernel with the carries.
+ * Queued on `stream`; hd_status reports HD_ERR_CORRUPT for a code 0 the
+ * outlier list lacks (its residue is taken as 0).  HD_ERR_ARG for invalid
  * parameters or alignment. */
 int hd_reconstruct_device(hd_ctx* ctx, const uint16_t* d_codes, const hd_lorenzo* L,
                           float* d_out, void* stream);

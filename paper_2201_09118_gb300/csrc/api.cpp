@@ -1357,7 +1357,6 @@ static int reconstruct_locked(hd_ctx* c, const uint16_t* d_codes, const hd_loren
   P.out_idx = L->out_idx;
   P.out_val = L->out_val;
   P.n_out = L->n_out;
-  P.timeout_cycles = 4000000000ull;  // about 2 s at the SM clock
   size_t need = 256;
   uint64_t zc = 1;
   // 3D grids with many slices and rows up to 1024 codes: one block per
@@ -1368,7 +1367,7 @@ static int reconstruct_locked(hd_ctx* c, const uint16_t* d_codes, const hd_loren
   if (one_d) {
     P.nx = n;
     P.ny = P.nz = 1;
-    need += 8ull * hd::lorenzo_tiles_1d(n);
+    need += 4ull * hd::lorenzo_tiles_1d(n);
   } else if (slice_path) {
     P.nx = ext[0];
     P.ny = ext[1];
@@ -1404,8 +1403,7 @@ static int reconstruct_locked(hd_ctx* c, const uint16_t* d_codes, const hd_loren
     c->rws_cap = cap;
   }
   P.err = reinterpret_cast<uint32_t*>(c->rws);
-  P.ticket = reinterpret_cast<uint32_t*>(c->rws + 128);
-  P.state = reinterpret_cast<unsigned long long*>(c->rws + 256);
+  P.tile_prefix = reinterpret_cast<int32_t*>(c->rws + 256);
   P.band = reinterpret_cast<int32_t*>(c->rws + 256);
   P.plane = reinterpret_cast<int32_t*>(c->rws + 256 + align_up(4ull * zc * P.nb * P.nx, 256));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1417,8 +1415,8 @@ static int reconstruct_locked(hd_ctx* c, const uint16_t* d_codes, const hd_loren
   if (e == cudaSuccess && c->profile) e = cudaEventRecord(e0, st);
   uint64_t launches = 0;
   if (one_d) {
-    if (e == cudaSuccess) e = hd::launch_lorenzo_1d(P, st);
-    launches = 1;
+    if (e == cudaSuccess) e = hd::launch_lorenzo_1d(P, c->num_sms, st);
+    launches = 3;
   } else if (slice_path) {
     P.z_lo = 0;
     P.z_hi = P.nz;

@@ -183,10 +183,8 @@ struct LorenzoParams {
   int32_t* band;             // per (slice of the launch, band, x): band column totals
   int32_t* plane;            // running z-sum of every (y, x) between launches [ny * nx]
   uint64_t z_lo, z_hi;
-  // 1D: decoupled look-back over tiles
-  unsigned long long* state; // per tile (zeroed before the launch)
-  uint32_t* ticket;          // tile counter (zeroed before the launch)
-  uint64_t timeout_cycles;
+  // 1D: exclusive prefix of the residue sums of each tile
+  int32_t* tile_prefix;
 };
 
 // Look-back state word: flag in bits 62..63, value in bits 0..61.

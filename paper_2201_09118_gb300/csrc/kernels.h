@@ -89,15 +89,15 @@ cudaError_t launch_histogram(const uint16_t* codes, uint64_t n, uint32_t alphabe
 cudaError_t launch_encode_count(const EncodeParams& e, int num_sms, cudaStream_t stream);
 cudaError_t launch_encode_write(const EncodeParams& e, int num_sms, cudaStream_t stream);
 
-// Lorenzo reconstruction (lorenzo.cu).  1D: one look-back pass over tiles of
-// codes (P.state[lorenzo_tiles_1d(n)] and P.ticket are cleared here).  2D/3D:
+// Lorenzo reconstruction (lorenzo.cu).  1D: tile sums, their scan and the
+// reconstruction pass (P.tile_prefix holds lorenzo_tiles_1d(n) entries).  2D/3D:
 // band, band-scan and z kernels over the slices [P.z_lo, P.z_hi); P.yb =
 // lorenzo_rows_per_band(nx); shared memory of the band kernel:
 // lorenzo_band_smem(P.yb, P.nx) (0 for rows up to 1024 codes).
 uint64_t lorenzo_tiles_1d(uint64_t n);
 uint32_t lorenzo_rows_per_band(uint64_t nx);
 size_t lorenzo_band_smem(uint32_t yb, uint64_t nx);
-cudaError_t launch_lorenzo_1d(const LorenzoParams& p, cudaStream_t stream);
+cudaError_t launch_lorenzo_1d(const LorenzoParams& p, int num_sms, cudaStream_t stream);
 cudaError_t launch_lorenzo_slices(const LorenzoParams& p, int num_sms, cudaStream_t stream);
 // Slice path for 3D grids: one block per slice (x and y prefixes), then the
 // z kernel; used when lorenzo_slice_path(nx, nz, num_sms).  Needs no band or

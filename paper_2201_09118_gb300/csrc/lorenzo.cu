@@ -7,8 +7,9 @@
 // q is the inclusive prefix sum of d along every axis, and the output is
 // float32(q) * float32(2 eb).
 //
-// 1D: one pass; tiles of 8192 codes take their prefix from a decoupled
-// look-back over per-tile states.
+// 1D: reduce, scan, reconstruct: residue sums of tiles of 8192 codes, an
+// exclusive scan of the tile sums, and a pass that scans each tile again
+// from its prefix and writes the floats (8 bytes per code moved).
 // 2D/3D: the prefix sums are separable, so per group of slices
 //   k_lorenzo_band      one block per band of yb rows of a slice: residues,
 //                       row sums (x) and the band's column sums (y) in shared
@@ -35,16 +36,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr uint64_t kWarpBandMaxRow = 1024;  // rows handled by one warp in registers
-
-__device__ __forceinline__ uint64_t ld_state(const unsigned long long* p) {
-  uint64_t v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_state(unsigned long long* p, uint64_t v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 
 // Residue of an outlier: binary search of position i in the outlier list.
 __device__ __noinline__ int32_t outlier_residue(const uint64_t* idx, const int32_t* val,
@@ -83,26 +74,21 @@ __device__ __forceinline__ int32_t warp_incl(int32_t v, int lane) {
 // Eight codes of a 16-byte vector -> residues.  Branch-free unless a code is
 // 0 (an outlier): one test per vector finds a zero half-word (it may also
 // fire for a zero low half-word's borrow, which only costs the slow path).
-__device__ __noinline__ void residues8_slow(const LorenzoParams& P, uint4 u, uint64_t i,
-                                            int32_t* d) {
-  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-  for (int k = 0; k < 4; ++k) {
-    d[2 * k] = residue(P, w[k] & 0xffffu, i + 2 * k);
-    d[2 * k + 1] = residue(P, w[k] >> 16, i + 2 * k + 1);
-  }
-}
-
 __device__ __forceinline__ bool has_zero_half(uint32_t w) {
   return ((w - 0x00010001u) & ~w & 0x80008000u) != 0;
 }
 
 __device__ __forceinline__ void residues8(const LorenzoParams& P, uint4 u, uint64_t i,
                                           int32_t* d) {
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
   if (has_zero_half(u.x) | has_zero_half(u.y) | has_zero_half(u.z) | has_zero_half(u.w)) {
-    residues8_slow(P, u, i, d);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      d[2 * k] = residue(P, w[k] & 0xffffu, i + 2 * k);
+      d[2 * k + 1] = residue(P, w[k] >> 16, i + 2 * k + 1);
+    }
     return;
   }
-  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     d[2 * k] = static_cast<int32_t>(w[k] & 0xffffu) - P.radius;
@@ -116,14 +102,73 @@ constexpr int k1Vec = 8;   // codes per 16-byte load
 constexpr int k1Rows = 4;  // loads per thread per tile
 constexpr uint64_t k1Tile = static_cast<uint64_t>(kThreads) * k1Vec * k1Rows;
 
-__global__ void __launch_bounds__(kThreads) k_lorenzo_1d(LorenzoParams P) {
-  __shared__ uint32_t s_tile;
-  __shared__ int32_t s_warp[k1Rows][kWarps];
-  __shared__ int32_t s_excl;
+// Tile sums of the residues (threads loop over the tiles).
+__global__ void __launch_bounds__(kThreads) k_lorenzo_1d_sums(LorenzoParams P, uint64_t tiles) {
+  __shared__ int32_t s_part[kWarps];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  if (t == 0) s_tile = atomicAdd(P.ticket, 1u);
+  for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const uint64_t base = tile * k1Tile;
+    int32_t sum = 0;
+    uint4 u[k1Rows];
+#pragma unroll
+    for (int r = 0; r < k1Rows; ++r) {
+      const uint64_t i0 = base + (static_cast<uint64_t>(r) * kThreads + t) * k1Vec;
+      if (i0 + k1Vec <= P.n) u[r] = __ldcs(reinterpret_cast<const uint4*>(P.codes + i0));
+    }
+#pragma unroll
+    for (int r = 0; r < k1Rows; ++r) {
+      const uint64_t i0 = base + (static_cast<uint64_t>(r) * kThreads + t) * k1Vec;
+      int32_t d[k1Vec];
+      if (i0 + k1Vec <= P.n) {
+        residues8(P, u[r], i0, d);
+      } else {
+#pragma unroll
+        for (int j = 0; j < k1Vec; ++j) d[j] = i0 + j < P.n ? residue(P, P.codes[i0 + j], i0 + j) : 0;
+      }
+#pragma unroll
+      for (int j = 0; j < k1Vec; ++j) sum += d[j];
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(~0u, sum, o);
+    if (lane == 0) s_part[w] = sum;
+    __syncthreads();
+    if (t == 0) {
+      int32_t total = 0;
+#pragma unroll
+      for (int k = 0; k < kWarps; ++k) total += s_part[k];
+      P.tile_prefix[tile] = total;
+    }
+    __syncthreads();
+  }
+}
+
+// Exclusive scan of the tile sums in place (one block).
+constexpr int k1ScanThreads = 1024;
+
+__global__ void __launch_bounds__(k1ScanThreads) k_lorenzo_1d_scan(int32_t* a, uint64_t tiles) {
+  __shared__ int32_t s_w[k1ScanThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const uint64_t per = (tiles + k1ScanThreads - 1) / k1ScanThreads;
+  const uint64_t lo = min(tiles, per * t), hi = min(tiles, lo + per);
+  int32_t sum = 0;
+  for (uint64_t k = lo; k < hi; ++k) sum += a[k];
+  const int32_t incl = warp_incl(sum, lane);
+  if (lane == 31) s_w[w] = incl;
   __syncthreads();
-  const uint64_t tile = s_tile;
+  int32_t run = incl - sum;
+  for (int k = 0; k < w; ++k) run += s_w[k];
+  for (uint64_t k = lo; k < hi; ++k) {
+    const int32_t v = a[k];
+    a[k] = run;
+    run += v;
+  }
+}
+
+// Reconstruction of one tile from its prefix.
+__global__ void __launch_bounds__(kThreads) k_lorenzo_1d(LorenzoParams P) {
+  __shared__ int32_t s_warp[k1Rows][kWarps];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const uint64_t tile = blockIdx.x;
   const uint64_t base = tile * k1Tile;
   // element (r, t, j) of the tile is base + (r * kThreads + t) * 8 + j
   int32_t v[k1Rows][k1Vec];
@@ -132,7 +177,7 @@ __global__ void __launch_bounds__(kThreads) k_lorenzo_1d(LorenzoParams P) {
   for (int r = 0; r < k1Rows; ++r) {
     const uint64_t i0 = base + (static_cast<uint64_t>(r) * kThreads + t) * k1Vec;
     if (i0 + k1Vec <= P.n) {
-      residues8(P, *reinterpret_cast<const uint4*>(P.codes + i0), i0, v[r]);
+      residues8(P, __ldcs(reinterpret_cast<const uint4*>(P.codes + i0)), i0, v[r]);
     } else {
 #pragma unroll
       for (int j = 0; j < k1Vec; ++j)
@@ -145,7 +190,7 @@ __global__ void __launch_bounds__(kThreads) k_lorenzo_1d(LorenzoParams P) {
     if (lane == 31) s_warp[r][w] = incl;
   }
   __syncthreads();
-  int32_t agg = 0, pre[k1Rows];
+  int32_t agg = P.tile_prefix[tile], pre[k1Rows];
 #pragma unroll
   for (int r = 0; r < k1Rows; ++r) {
 #pragma unroll
@@ -154,57 +199,17 @@ __global__ void __launch_bounds__(kThreads) k_lorenzo_1d(LorenzoParams P) {
       agg += s_warp[r][k];
     }
   }
-  if (w == 0) {
-    int32_t excl = 0;
-    if (tile == 0) {
-      if (lane == 0) st_state(P.state, kStateInc | static_cast<uint32_t>(agg));
-    } else {
-      if (lane == 0) st_state(P.state + tile, kStateAgg | static_cast<uint32_t>(agg));
-      int64_t j = static_cast<int64_t>(tile) - 1;
-      const uint64_t t0 = clock64();
-      bool ok = true;
-      while (true) {
-        const int64_t idx = j - lane;
-        const uint64_t s = idx >= 0 ? ld_state(P.state + idx) : kStateInc;
-        const unsigned inc = __ballot_sync(~0u, (s & kStateInc) != 0);
-        const unsigned ready = __ballot_sync(~0u, (s >> 62) != 0);
-        // lanes up to the nearest inclusive state (or all) must be ready
-        const unsigned need = inc ? ((inc & (0u - inc)) << 1) - 1u : ~0u;
-        if ((ready & need) != need) {
-          if (__any_sync(~0u, static_cast<uint64_t>(clock64()) - t0 > P.timeout_cycles)) {
-            ok = false;
-            break;
-          }
-          __nanosleep(64);
-          continue;
-        }
-        int32_t part = ((need >> lane) & 1u) ? static_cast<int32_t>(static_cast<uint32_t>(s)) : 0;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(~0u, part, o);
-        excl += part;
-        if (inc) break;
-        j -= 32;
-      }
-      if (lane == 0) {
-        if (!ok) atomicOr(P.err, kErrTimeout);
-        st_state(P.state + tile, kStateInc | static_cast<uint32_t>(excl + agg));
-      }
-    }
-    if (lane == 0) s_excl = excl;
-  }
-  __syncthreads();
-  const int32_t excl = s_excl;
 #pragma unroll
   for (int r = 0; r < k1Rows; ++r) {
     const uint64_t i0 = base + (static_cast<uint64_t>(r) * kThreads + t) * k1Vec;
-    const int32_t off = excl + pre[r] + ex[r];
+    const int32_t off = pre[r] + ex[r];
     float o[k1Vec];
 #pragma unroll
     for (int j = 0; j < k1Vec; ++j) o[j] = value(P, off + v[r][j]);
     if (i0 + k1Vec <= P.n) {
       float4* dst = reinterpret_cast<float4*>(P.out + i0);
-      dst[0] = make_float4(o[0], o[1], o[2], o[3]);
-      dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+      __stcs(dst, make_float4(o[0], o[1], o[2], o[3]));
+      __stcs(dst + 1, make_float4(o[4], o[5], o[6], o[7]));
     } else {
 #pragma unroll
       for (int j = 0; j < k1Vec; ++j)
@@ -288,24 +293,152 @@ __global__ void __launch_bounds__(kThreads) k_lorenzo_band(LorenzoParams P) {
   }
 }
 
-// Rows up to 1024 codes: one warp per band, everything in registers.  Lane l
-// holds the 8-code chunks l, l + 32, .. of a row; a row's prefix is a lane
-// scan per chunk plus one warp scan per chunk column, and the band's column
-// sums run in registers while the rows stream through.  No shared memory and
-// no barriers.  R rows of raw codes are loaded before any is processed (all
-// of a band of R rows: R * K 16-byte loads in flight per lane).  Warps loop
-// over the bands of the launch (the grid is one resident wave).
+// Rows up to 1024 codes, one warp per band of rows, everything in
+// registers: lane l holds the 8-code chunks l, l + 32, .. of a row; a row's
+// prefix is a lane scan per chunk plus one warp scan per chunk column, and the
+// column sums run in registers while the rows stream through (no shared
+// memory, no barriers).  R rows of raw codes are loaded before any is
+// processed.  `col` enters with the band's y carry (x prefix included) and
+// leaves with the prefix of the band's last row.
+template <int K, bool VEC>
+__device__ __forceinline__ void load_row(const LorenzoParams& P, int lane, uint64_t row0,
+                                         uint32_t r, uint32_t h, uint4 (&raw)[K]) {
+  const uint32_t nx = static_cast<uint32_t>(P.nx);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint32_t x = 8u * (lane + 32u * k);
+    raw[k] = VEC && r < h && x < nx
+                 ? __ldcg(reinterpret_cast<const uint4*>(P.codes + row0 +
+                                                         static_cast<uint64_t>(r) * nx + x))
+                 : make_uint4(0, 0, 0, 0);
+  }
+}
+
+template <int K, bool VEC>
+__device__ __forceinline__ void row_residues(const LorenzoParams& P, int lane, uint64_t rs,
+                                             const uint4 (&raw)[K], int k, int32_t (&v)[8]) {
+  const uint32_t nx = static_cast<uint32_t>(P.nx);
+  const uint32_t x = 8u * (lane + 32u * k);
+  if (VEC) {
+    if (x < nx) {
+      residues8(P, raw[k], rs + x, v);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = 0;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      v[j] = x + j < nx ? residue(P, P.codes[rs + x + j], rs + x + j) : 0;
+  }
+}
+
+// Rows stream through a ring of R rows of raw codes: the load of row r + R
+// is issued as soon as row r has been taken out of the ring.
+template <int K, bool VEC, int R>
+__device__ __forceinline__ void warp_rows(const LorenzoParams& P, int lane, uint64_t row0,
+                                          uint32_t h, int32_t (&col)[K][8]) {
+  const uint32_t nx = static_cast<uint32_t>(P.nx);
+  int32_t* inter = reinterpret_cast<int32_t*>(P.out);
+  uint4 raw[R][K];
+#pragma unroll
+  for (int p = 0; p < R; ++p) load_row<K, VEC>(P, lane, row0, p, h, raw[p]);
+  for (uint32_t r0 = 0; r0 < h; r0 += R) {
+#pragma unroll
+    for (int p = 0; p < R; ++p) {
+      const uint32_t r = r0 + p;
+      if (r >= h) break;
+      const uint64_t rs = row0 + static_cast<uint64_t>(r) * nx;
+      uint4 cur[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) cur[k] = raw[p][k];
+      load_row<K, VEC>(P, lane, row0, r + R, h, raw[p]);
+      int32_t carry = 0;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const uint32_t x = 8u * (lane + 32u * k);
+        int32_t v[8];
+        row_residues<K, VEC>(P, lane, rs, cur, k, v);
+#pragma unroll
+        for (int j = 1; j < 8; ++j) v[j] += v[j - 1];
+        const int32_t incl = warp_incl(v[7], lane);
+        const int32_t e = incl - v[7] + carry;
+        carry += __shfl_sync(~0u, incl, 31);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) col[k][j] += v[j] + e;
+        if (VEC) {
+          if (x < nx) {
+            int4* dst = reinterpret_cast<int4*>(inter + rs + x);
+            dst[0] = make_int4(col[k][0], col[k][1], col[k][2], col[k][3]);
+            dst[1] = make_int4(col[k][4], col[k][5], col[k][6], col[k][7]);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (x + j < nx) inter[rs + x + j] = col[k][j];
+        }
+      }
+    }
+  }
+}
+
+// Residue sums per column over h rows (no scans), through the same ring.
+template <int K, bool VEC, int R>
+__device__ __forceinline__ void warp_colsums(const LorenzoParams& P, int lane, uint64_t row0,
+                                             uint32_t h, int32_t (&acc)[K][8]) {
+  const uint32_t nx = static_cast<uint32_t>(P.nx);
+  uint4 raw[R][K];
+#pragma unroll
+  for (int p = 0; p < R; ++p) load_row<K, VEC>(P, lane, row0, p, h, raw[p]);
+  for (uint32_t r0 = 0; r0 < h; r0 += R) {
+#pragma unroll
+    for (int p = 0; p < R; ++p) {
+      const uint32_t r = r0 + p;
+      if (r >= h) break;
+      const uint64_t rs = row0 + static_cast<uint64_t>(r) * nx;
+      uint4 cur[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) cur[k] = raw[p][k];
+      load_row<K, VEC>(P, lane, row0, r + R, h, raw[p]);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        int32_t v[8];
+        row_residues<K, VEC>(P, lane, rs, cur, k, v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[k][j] += v[j];
+      }
+    }
+  }
+}
+
+// x prefix of a row held as in warp_rows (in place).
+template <int K>
+__device__ __forceinline__ void warp_row_prefix(int lane, int32_t (&a)[K][8]) {
+  int32_t carry = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int j = 1; j < 8; ++j) a[k][j] += a[k][j - 1];
+    const int32_t incl = warp_incl(a[k][7], lane);
+    const int32_t e = incl - a[k][7] + carry;
+    carry += __shfl_sync(~0u, incl, 31);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[k][j] += e;
+  }
+}
+
+// Band path: warps loop over the bands of the launch (the grid is one
+// resident wave); each writes its band's local prefix and column totals.
 constexpr int kWarpBandThreads = 128;
 
 template <int K, bool VEC, int R>
-__global__ void __launch_bounds__(kWarpBandThreads, K <= 2 ? 5 : 3)
+__global__ void __launch_bounds__(kWarpBandThreads, K <= 2 ? 4 : 3)
     k_lorenzo_warpband(LorenzoParams P) {
   constexpr int W = kWarpBandThreads / 32;
   const int lane = threadIdx.x & 31;
   const uint64_t total = (P.z_hi - P.z_lo) * P.nb;
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * W;
   const uint32_t nx = static_cast<uint32_t>(P.nx);
-  int32_t* inter = reinterpret_cast<int32_t*>(P.out);
   for (uint64_t gw = static_cast<uint64_t>(blockIdx.x) * W + (threadIdx.x >> 5); gw < total;
        gw += stride) {
     const uint64_t zz = gw / P.nb;
@@ -318,62 +451,7 @@ __global__ void __launch_bounds__(kWarpBandThreads, K <= 2 ? 5 : 3)
     for (int k = 0; k < K; ++k)
 #pragma unroll
       for (int j = 0; j < 8; ++j) col[k][j] = 0;
-    for (uint32_t r0 = 0; r0 < h; r0 += R) {
-      uint4 raw[R][K];
-      if (VEC) {
-#pragma unroll
-        for (int p = 0; p < R; ++p)
-#pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const uint32_t x = 8u * (lane + 32u * k);
-            raw[p][k] = r0 + p < h && x < nx
-                            ? __ldcs(reinterpret_cast<const uint4*>(
-                                  P.codes + row0 + static_cast<uint64_t>(r0 + p) * nx + x))
-                            : make_uint4(0, 0, 0, 0);
-          }
-      }
-#pragma unroll
-      for (int p = 0; p < R; ++p) {
-        if (r0 + p >= h) break;
-        const uint64_t rs = row0 + static_cast<uint64_t>(r0 + p) * nx;
-        int32_t carry = 0;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const uint32_t x = 8u * (lane + 32u * k);
-          int32_t v[8];
-          if (VEC) {
-            if (x < nx) {
-              residues8(P, raw[p][k], rs + x, v);
-            } else {
-#pragma unroll
-              for (int j = 0; j < 8; ++j) v[j] = 0;
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              v[j] = x + j < nx ? residue(P, P.codes[rs + x + j], rs + x + j) : 0;
-          }
-#pragma unroll
-          for (int j = 1; j < 8; ++j) v[j] += v[j - 1];
-          const int32_t incl = warp_incl(v[7], lane);
-          const int32_t e = incl - v[7] + carry;
-          carry += __shfl_sync(~0u, incl, 31);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) col[k][j] += v[j] + e;
-          if (VEC) {
-            if (x < nx) {
-              int4* dst = reinterpret_cast<int4*>(inter + rs + x);
-              dst[0] = make_int4(col[k][0], col[k][1], col[k][2], col[k][3]);
-              dst[1] = make_int4(col[k][4], col[k][5], col[k][6], col[k][7]);
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              if (x + j < nx) inter[rs + x + j] = col[k][j];
-          }
-        }
-      }
-    }
+    warp_rows<K, VEC, R>(P, lane, row0, h, col);
     int32_t* band = P.band + gw * P.nx;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -390,6 +468,61 @@ __global__ void __launch_bounds__(kWarpBandThreads, K <= 2 ? 5 : 3)
           if (x + j < nx) band[x + j] = col[k][j];
       }
     }
+  }
+}
+
+// Slice path (3D grids with many slices, rows up to 1024 codes): one block of
+// kSliceWarps warps per slice, warp w taking an equal share of its rows.
+// Each warp first sums the residues of its rows per column (no scans) into
+// shared memory; after the one barrier, a warp's y carry is the x prefix of
+// the column sums of the warps above it, and it streams its rows as a band
+// warp (their codes read again, now from L2), writing the slice's x-y prefix
+// as int32.  The z kernel follows.
+constexpr int kSliceWarps = 4;
+constexpr int kSliceThreads = 32 * kSliceWarps;
+
+template <int K, bool VEC, int R>
+__global__ void __launch_bounds__(kSliceThreads, 4) k_lorenzo_slice(LorenzoParams P) {
+  extern __shared__ int4 s_raw[];
+  int32_t* s_tot = reinterpret_cast<int32_t*>(s_raw);  // [kSliceWarps][nx]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t nx = static_cast<uint32_t>(P.nx);
+  const uint32_t ny = static_cast<uint32_t>(P.ny);
+  const uint32_t rpw = (ny + kSliceWarps - 1) / kSliceWarps;
+  const uint32_t r_lo = min(ny, w * rpw);
+  const uint32_t h = min(ny, r_lo + rpw) - r_lo;
+  for (uint64_t z = P.z_lo + blockIdx.x; z < P.z_hi; z += gridDim.x) {
+    const uint64_t row0 = (z * P.ny + r_lo) * P.nx;
+    int32_t a[K][8];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) a[k][j] = 0;
+    warp_colsums<K, VEC, R>(P, lane, row0, h, a);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint32_t x = 8u * (lane + 32u * k);
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (x + j < nx) s_tot[w * nx + x + j] = a[k][j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) a[k][j] = 0;
+    for (int v = 0; v < w; ++v) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const uint32_t x = 8u * (lane + 32u * k);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (x + j < nx) a[k][j] += s_tot[v * nx + x + j];
+      }
+    }
+    __syncthreads();  // s_tot is rewritten for the next slice
+    warp_row_prefix<K>(lane, a);
+    warp_rows<K, VEC, R>(P, lane, row0, h, a);
   }
 }
 
@@ -509,96 +642,6 @@ __global__ void __launch_bounds__(kColThreads) k_lorenzo_zscan(LorenzoParams P) 
   }
 }
 
-// Slice path (3D grids with many slices, rows of at most 1024 codes): one
-// block per slice computes its prefix along x and y; rows stream through
-// with kSliceAhead rows of codes loaded ahead.  Thread t holds columns
-// [4t, 4t + 4): a lane scan, a warp scan and one cross-warp step per row
-// (one barrier, the warp totals double-buffered); the y sums run in
-// registers.  Writes the slice as int32 into the output buffer; the z kernel
-// follows.
-constexpr int kSliceAhead = 16;
-constexpr int kSliceMaxThreads = 256;
-
-template <bool VEC>
-__global__ void __launch_bounds__(kSliceMaxThreads) k_lorenzo_slice(LorenzoParams P) {
-  __shared__ int32_t s_w[2][kSliceMaxThreads / 32];
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int nw = blockDim.x >> 5;
-  const uint32_t nx = static_cast<uint32_t>(P.nx);
-  const uint32_t ny = static_cast<uint32_t>(P.ny);
-  const uint32_t x = 4u * t;
-  const bool mine = x < nx;
-  int32_t* inter = reinterpret_cast<int32_t*>(P.out);
-  for (uint64_t z = P.z_lo + blockIdx.x; z < P.z_hi; z += gridDim.x) {
-    const uint64_t base = z * P.ny * P.nx;
-    int32_t col[4] = {0, 0, 0, 0};
-    uint2 ring[kSliceAhead];
-    const uint32_t centre = static_cast<uint32_t>(P.radius) * 0x10001u;  // two residues 0
-    auto load = [&](uint32_t r) {
-      uint2 u = make_uint2(centre, centre);
-      if (r < ny && mine) {
-        const uint64_t i = base + static_cast<uint64_t>(r) * nx + x;
-        if (VEC) {
-          u = __ldcs(reinterpret_cast<const uint2*>(P.codes + i));
-        } else {
-          uint32_t h[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            h[j] = x + j < nx ? P.codes[i + j] : static_cast<uint32_t>(P.radius);
-          u = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
-        }
-      }
-      return u;
-    };
-#pragma unroll
-    for (int p = 0; p < kSliceAhead; ++p) ring[p] = load(p);
-    for (uint32_t r0 = 0; r0 < ny; r0 += kSliceAhead) {
-#pragma unroll
-      for (int p = 0; p < kSliceAhead; ++p) {
-        const uint32_t r = r0 + p;
-        if (r >= ny) break;  // uniform across the block
-        const uint64_t i = base + static_cast<uint64_t>(r) * nx + x;
-        const uint2 u = ring[p];
-        ring[p] = load(r + kSliceAhead);
-        int32_t v[4];
-        if (has_zero_half(u.x) | has_zero_half(u.y)) {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const uint32_t c = (j < 2 ? u.x : u.y) >> (16 * (j & 1)) & 0xffffu;
-            v[j] = mine && x + j < nx ? residue(P, c, i + j) : 0;
-          }
-        } else {
-          v[0] = static_cast<int32_t>(u.x & 0xffffu) - P.radius;
-          v[1] = static_cast<int32_t>(u.x >> 16) - P.radius;
-          v[2] = static_cast<int32_t>(u.y & 0xffffu) - P.radius;
-          v[3] = static_cast<int32_t>(u.y >> 16) - P.radius;
-        }
-        v[1] += v[0];
-        v[2] += v[1];
-        v[3] += v[2];
-        const int32_t incl = warp_incl(v[3], lane);
-        if (lane == 31) s_w[r & 1][w] = incl;
-        __syncthreads();
-        int32_t e = incl - v[3];
-        for (int k = 0; k < nw; ++k)
-          if (k < w) e += s_w[r & 1][k];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) col[j] += v[j] + e;
-        if (mine) {
-          if (VEC) {
-            *reinterpret_cast<int4*>(inter + i) = make_int4(col[0], col[1], col[2], col[3]);
-          } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-              if (x + j < nx) inter[i + j] = col[j];
-          }
-        }
-      }
-    }
-    __syncthreads();  // s_w is reused by the next slice
-  }
-}
-
 // Blocks of one resident wave (at most `want`) for a kernel.
 template <class Kernel>
 unsigned wave_blocks(Kernel kernel, int threads, size_t smem, int num_sms, uint64_t want) {
@@ -626,12 +669,12 @@ size_t lorenzo_band_smem(uint32_t yb, uint64_t nx) {
   return nx <= kWarpBandMaxRow ? 0 : 4ull * yb * nx;
 }
 
-cudaError_t launch_lorenzo_1d(const LorenzoParams& P, cudaStream_t st) {
+cudaError_t launch_lorenzo_1d(const LorenzoParams& P, int num_sms, cudaStream_t st) {
   const uint64_t tiles = lorenzo_tiles_1d(P.n);
   if (!tiles) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(P.state, 0, 8ull * tiles, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(P.ticket, 0, 4, st);
-  if (e != cudaSuccess) return e;
+  k_lorenzo_1d_sums<<<wave_blocks(k_lorenzo_1d_sums, kThreads, 0, num_sms, tiles), kThreads, 0,
+                      st>>>(P, tiles);
+  k_lorenzo_1d_scan<<<1, k1ScanThreads, 0, st>>>(P.tile_prefix, tiles);
   k_lorenzo_1d<<<static_cast<unsigned>(tiles), kThreads, 0, st>>>(P);
   return cudaGetLastError();
 }
@@ -665,15 +708,34 @@ void launch_warpband(const LorenzoParams& P, int num_sms, cudaStream_t st) {
 }
 
 bool lorenzo_slice_path(uint64_t nx, uint64_t nz, int num_sms) {
-  return nx <= 4ull * kSliceMaxThreads && nz >= 2ull * static_cast<uint64_t>(num_sms);
+  return nx <= kWarpBandMaxRow && nz >= 2ull * static_cast<uint64_t>(num_sms);
+}
+
+template <int K, int R>
+void launch_slice(const LorenzoParams& P, int num_sms, cudaStream_t st) {
+  const size_t smem = 4ull * kSliceWarps * P.nx;
+  const uint64_t nzc = P.z_hi - P.z_lo;
+  if (P.nx % 8 == 0) {
+    auto k = k_lorenzo_slice<K, true, R>;
+    k<<<wave_blocks(k, kSliceThreads, smem, num_sms, nzc), kSliceThreads, smem, st>>>(P);
+  } else {
+    auto k = k_lorenzo_slice<K, false, 1>;
+    k<<<wave_blocks(k, kSliceThreads, smem, num_sms, nzc), kSliceThreads, smem, st>>>(P);
+  }
 }
 
 cudaError_t launch_lorenzo_whole_slices(const LorenzoParams& P, int num_sms, cudaStream_t st) {
   const uint64_t nzc = P.z_hi - P.z_lo;
   if (!nzc || !P.ny || !P.nx) return cudaSuccess;
-  const int threads = static_cast<int>(((P.nx + 3) / 4 + 31) / 32 * 32);
-  auto k = P.nx % 4 == 0 ? k_lorenzo_slice<true> : k_lorenzo_slice<false>;
-  k<<<wave_blocks(k, threads, 0, num_sms, nzc), threads, 0, st>>>(P);
+  const uint64_t chunks = (P.nx + 255) / 256;
+  if (chunks == 1)
+    launch_slice<1, 4>(P, num_sms, st);
+  else if (chunks == 2)
+    launch_slice<2, 4>(P, num_sms, st);
+  else if (chunks == 3)
+    launch_slice<3, 2>(P, num_sms, st);
+  else
+    launch_slice<4, 1>(P, num_sms, st);
   launch_zscan<false>(P, num_sms, st);
   return cudaGetLastError();
 }
@@ -688,9 +750,9 @@ cudaError_t launch_lorenzo_slices(const LorenzoParams& P, int num_sms, cudaStrea
     else if (chunks == 2)
       launch_warpband<2, 4>(P, num_sms, st);
     else if (chunks == 3)
-      launch_warpband<3, 4>(P, num_sms, st);
+      launch_warpband<3, 2>(P, num_sms, st);
     else
-      launch_warpband<4, 4>(P, num_sms, st);
+      launch_warpband<4, 2>(P, num_sms, st);
   } else {
     const size_t smem = lorenzo_band_smem(P.yb, P.nx);
     const bool vec = P.nx % 8 == 0;
