@@ -322,8 +322,9 @@ def run_decompress(hd, torch, ctx, field, dec_codes, g, stream, flush, steps: in
     L = hd.lorenzo_params(dims, 512, g["eb"], idx, val)
     recon_ms = timed(lambda: ctx.reconstruct(dec_codes, L, fout, stream))
     ok = ctx.status(stream) == 0
+    # the band path (groups of 64 slices, or all slices in one group) for comparison
     sweep = {}
-    for zc in (1, 8, 16, 64, side):
+    for zc in (64, side):
         Lz = hd.lorenzo_params(dims, 512, g["eb"], idx, val, zc)
         sweep[str(zc)] = timed(lambda: ctx.reconstruct(dec_codes, Lz, fout, stream))
     dec_ms = timed(lambda: ctx.decompress(field, L, fout, stream))
@@ -341,7 +342,7 @@ def run_decompress(hd, torch, ctx, field, dec_codes, g, stream, flush, steps: in
             "value": 4.0 * n / (dec_ms * 1e-3) / 1e9,
             "unit": "GB/s (float32 values out, decode + reconstruction)",
             "decompress_ms": dec_ms, "reconstruct_ms": recon_ms,
-            "reconstruct_slice_groups_ms": sweep,
+            "reconstruct_band_path_ms_by_slice_group": sweep,
             "reconstruct_roofline": {"bound": "hbm", "achieved": alg / (recon_ms * 1e-3) / 1e9,
                                      "peak": peak, "unit": "GB/s",
                                      "frac": alg / (recon_ms * 1e-3) / 1e9 / peak,
@@ -694,11 +695,44 @@ def run_gpu(args):
     return 0
 
 
+def run_profile_recon(args):
+    """Reconstructs the workload's codes `steps` times after `warmup` (for
+    profiler captures); prints one timing line, no bench line."""
+    import torch
+    from paper_2201_09118_gb300 import hd
+    torch.cuda.set_device(0)
+    g = workload_quantized(args.side, seed=1001)
+    n = g["codes"].size
+    codes = torch.from_numpy(g["codes"].view(np.int16)).cuda()
+    idx = torch.from_numpy(g["out_idx"].view(np.int64)).cuda()
+    val = torch.from_numpy(g["out_val"]).cuda()
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    ctx = hd.Context(0)
+    side = args.side
+    L = hd.lorenzo_params((side, side, side), 512, g["eb"], idx, val)
+    for _ in range(args.warmup):
+        ctx.reconstruct(codes, L, out)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        ctx.reconstruct(codes, L, out)
+    b.record()
+    b.synchronize()
+    st = ctx.status()
+    print(json.dumps({"profile_case": "recon", "n_codes": n,
+                      "ms": a.elapsed_time(b) / max(1, args.steps), "ok": st == 0}), flush=True)
+    return 0 if st == 0 else 1
+
+
 def run_profile_case(args):
     """Decodes one strategy `steps` times after `warmup` (for profiler
     captures); prints one timing line, no bench line."""
     import torch
     from paper_2201_09118_gb300 import hd
+    if args.profile_strategy == "recon":
+        return run_profile_recon(args)
     torch.cuda.set_device(0)
     codes = workload_codes(args.side, seed=1001)
     n = codes.size
@@ -741,8 +775,9 @@ def main():
                     help="skip the batched (256 fields) and served (request trace) legs")
     ap.add_argument("--batch-fields", dest="batch_fields", type=int, default=256)
     ap.add_argument("--requests", type=int, default=10000)
-    ap.add_argument("--profile-strategy", choices=["gap", "selfsync"], default=None,
-                    help="decode one strategy only and print its kernel time (profiler runs)")
+    ap.add_argument("--profile-strategy", choices=["gap", "selfsync", "recon"], default=None,
+                    help="decode one strategy (or reconstruct the decoded codes) only and "
+                         "print its time (profiler runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
