@@ -350,6 +350,59 @@ def run_decompress(hd, torch, ctx, field, dec_codes, g, stream, flush, steps: in
             "status_ok": bool(ok), "within_error_bound": bound_ok}
 
 
+def run_decompress_1d(hd, torch, ctx_dev, stream, flush, steps: int = 5, n: int = 280_953_867):
+    """Decode + reconstruction of a 1D field of the HACC particle count: the
+    fused path (values straight from the decoder) against decode into codes
+    then reconstruction, and the two halves alone."""
+    import synth
+    f1 = synth.fourier_field((n,), noise=1e-4, kmax=8, seed=1002)
+    g = synth.lorenzo_quantize(f1, 1e-4, radius=512)
+    del f1
+    codes = g["codes"]
+    lengths = hd.hd_build_codebook(codes, 1024, 32)
+    enc = hd.hd_encode(codes, lengths, 128)
+    dev = f"cuda:{ctx_dev}"
+    f = hd.DeviceField.upload(enc, lengths, n, device=dev)
+    idx = torch.from_numpy(g["out_idx"].view(np.int64)).to(dev)
+    val = torch.from_numpy(g["out_val"]).to(dev)
+    vals = torch.empty(n, dtype=torch.float32, device=dev)
+    dec = torch.empty(n, dtype=torch.int16, device=dev)
+    ctx = hd.Context(ctx_dev)
+    ctx.autotune([f], [dec], stream)
+
+    def timed(fn):
+        fn()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    Lf = hd.lorenzo_params((n,), 512, g["eb"], idx, val)
+    Ls = hd.lorenzo_params((n,), 512, g["eb"], idx, val, separate=True)
+    fused = timed(lambda: ctx.decompress(f, Lf, vals, stream))
+    ok = ctx.status(stream) == 0
+    first = vals[:1 << 20].clone()
+    separate = timed(lambda: ctx.decompress(f, Ls, vals, stream))
+    ok = ok and ctx.status(stream) == 0 and bool(torch.equal(first, vals[:1 << 20]))
+    decode = timed(lambda: ctx.decode(f, dec, stream))
+    recon = timed(lambda: ctx.reconstruct(dec, Lf, vals, stream))
+    ok = ok and ctx.status(stream) == 0
+    ctx.close()
+    return {"workload": f"{n} 1D codes (rel. error bound 1e-4, radius 512, "
+                        f"{enc['nbits'] / n:.2f} bits/code, {g['out_idx'].size} outliers)",
+            "value": 4.0 * n / (fused * 1e-3) / 1e9,
+            "unit": "GB/s (float32 values out, fused decode + reconstruction)",
+            "fused_ms": fused, "separate_ms": separate, "decode_ms": decode,
+            "reconstruct_ms": recon, "status_ok": bool(ok)}
+
+
 def mixed_cr_workload(n_seg: int = 32, seg: int = 1 << 21, seed: int = 1005):
     """A 1D field whose compressibility changes along it (segments quantized at
     error bounds 1e-2 .. 1e-6), for the window-class ablation."""
@@ -651,6 +704,8 @@ def run_gpu(args):
     extra = {}
     extra["decompress"] = run_decompress(hd, torch, ctx, field, out, quant, stream, flush)
     quant.pop("field", None)
+    if fields_h is not None:
+        extra["decompress_1d"] = run_decompress_1d(hd, torch, dev, stream, flush)
     if fields_h is not None:
         extra["cr_class_ablation"] = run_cr_ablation(hd, torch, dev, stream, flush, mixed_codes)
         batched, dev_fields = run_batched(hd, torch, dev, stream, flush, fields_h, 3)

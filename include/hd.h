@@ -337,6 +337,10 @@ typedef struct hd_lorenzo {
   uint32_t band_rows;      /* band path: rows per band, 1 .. 64 (0 = 8 for rows
                               up to 1024 codes, else as many as 64 KB of shared
                               memory holds, at most 32) */
+  uint32_t separate;       /* hd_decompress_device, 1D gap-array fields: 1 = decode
+                              into codes, then reconstruct; 0 = fused (values
+                              straight from the decoder) */
+  uint32_t pad;
 } hd_lorenzo;
 
 /* Reconstructs dims[0]*..*dims[ndim-1] float32 values into d_out (device,
@@ -356,9 +360,14 @@ typedef struct hd_lorenzo {
 int hd_reconstruct_device(hd_ctx* ctx, const uint16_t* d_codes, const hd_lorenzo* L,
                           float* d_out, void* stream);
 
-/* Decompression: hd_decode of f (device field, f->n = the grid size) into a
- * context-owned code buffer, then hd_reconstruct_device into d_out.  One
- * status for both through hd_status. */
+/* Decompression of f (device field, f->n = the grid size) into float32
+ * values d_out (device, 16-byte aligned).  1D gap-array fields (unless
+ * L->separate): fused -- the count kernel also sums each tile's residues,
+ * the tile scan scans them, a tile kernel adds the outliers' corrections and
+ * the decode-and-write kernel turns each output window into values (a block
+ * scan from the tile's q) instead of storing codes; no codes reach HBM.
+ * Otherwise hd_decode into a context-owned code buffer, then
+ * hd_reconstruct_device.  One status for both through hd_status. */
 int hd_decompress_device(hd_ctx* ctx, const hd_field* f, const hd_lorenzo* L, float* d_out,
                          void* stream);
 

@@ -433,20 +433,39 @@ int queue_cr_classes(hd_ctx* c, hd::DecodeParams dp, const Prepared& P, char* cl
   return HD_OK;
 }
 
+// Decode + 1D Lorenzo reconstruction: where the values go and the outliers.
+struct ValueArgs {
+  float* vout;
+  int32_t radius;
+  float ebx2;
+  const uint64_t* out_idx;
+  const int32_t* out_val;
+  uint64_t n_out;
+  uint32_t* verr;  // error word of the reconstruction (cleared by the caller)
+};
+
 // Queues a decode of fields that all use the same strategy with direct
-// kernel launches (sizes as kernel parameters).
+// kernel launches (sizes as kernel parameters).  With `va` (one gap-array
+// field): values instead of codes.
 int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape& shape,
-                 bool self_sync, bool sync_only, cudaStream_t st) {
+                 bool self_sync, bool sync_only, cudaStream_t st,
+                 const ValueArgs* va = nullptr) {
   const uint32_t nf = static_cast<uint32_t>(descs.size());
   Prepared P;
   int rc = prepare_launch(c, descs, shape, self_sync, P);
   if (rc) return rc;
   const Layout L = make_layout(nf, P.tiles, P.subs, P.tab_bytes, P.s, self_sync,
                                self_sync && !sync_only);
-  const uint32_t nclass = self_sync ? 0u : c->cfg.cr_classes;
+  const uint32_t nclass = self_sync || va ? 0u : c->cfg.cr_classes;
   const size_t cls_off = L.total;  // CR classes: counts, then one tile list per class
   const size_t cls_bytes = nclass ? 256 + 4ull * nclass * P.tiles : 0;
-  rc = ensure_ws(c, L.total + cls_bytes);
+  // values: tile residue sums, q bases, outlier bases, outlier corrections
+  const size_t rs_off = align_up(L.total, 256);
+  const size_t qb_off = align_up(rs_off + 4ull * P.tiles, 256);
+  const size_t ob_off = align_up(qb_off + 8ull * (P.tiles + 1), 256);
+  const size_t co_off = align_up(ob_off + 8ull * (P.tiles + 1), 256);
+  const size_t need = va ? co_off + 4ull * (va->n_out + 1) : L.total + cls_bytes;
+  rc = ensure_ws(c, need);
   if (rc) return rc;
   char* ws = c->ws;
   bind_descs(descs, ws, L, P, self_sync, sync_only);
@@ -456,6 +475,19 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
   hd::PrepParams pp;
   hd::DecodeParams dp;
   make_params(descs, ws, L, P.s, self_sync, false, nf, P.tiles, pp, dp);
+  if (va) {
+    dp.tile_rsum = reinterpret_cast<uint32_t*>(ws + rs_off);
+    dp.tile_qbase = reinterpret_cast<uint64_t*>(ws + qb_off);
+    dp.tile_obase = reinterpret_cast<uint64_t*>(ws + ob_off);
+    dp.out_corr = reinterpret_cast<const int32_t*>(ws + co_off);
+    dp.vout = va->vout;
+    dp.radius = va->radius;
+    dp.ebx2 = va->ebx2;
+    dp.out_idx = va->out_idx;
+    dp.out_val = va->out_val;
+    dp.n_out = va->n_out;
+    dp.verr = va->verr;
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->profile) {
     e0 = next_event(c);
@@ -468,6 +500,10 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
     if (self_sync) {
       e = hd::launch_sync(dp, P.s, c->num_sms, st);
       if (e == cudaSuccess && !sync_only) e = hd::launch_write(dp, P.s, c->num_sms, st);
+    } else if (va) {
+      e = hd::launch_outlier_prefix(va->out_val, va->n_out, va->radius,
+                                    reinterpret_cast<int32_t*>(ws + co_off), st);
+      if (e == cudaSuccess) e = hd::launch_decode_values(dp, P.s, c->num_sms, st);
     } else if (nclass) {
       rc = queue_cr_classes(c, dp, P, ws + cls_off, nclass, st);
       if (rc) return rc;
@@ -477,7 +513,7 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
   }
   if (c->profile) cudaEventRecord(e1, st);
   if (e != cudaSuccess) return HD_ERR_CUDA;
-  c->launches += kernels_per_launch(self_sync, sync_only);
+  c->launches += kernels_per_launch(self_sync, sync_only) + (va ? 2 : 0);
   c->err_off = L.err;
   c->err_count = nf;
   c->recon_active = false;
@@ -1315,6 +1351,88 @@ int hd_encode_device(hd_ctx* c, const uint16_t* d_codes, uint64_t n, const uint8
 static constexpr uint64_t kReconMaxRow = 49152;          // 2D/3D row limit (band shared memory)
 static constexpr uint64_t kReconGroupBytes = 32ull << 20;  // int32 intermediate per slice group
 
+static int ensure_rws(hd_ctx* c, size_t need) {
+  if (need <= c->rws_cap) return HD_OK;
+  if (c->rws) {
+    cudaDeviceSynchronize();
+    cudaFree(c->rws);
+    c->rws = nullptr;
+    c->rws_cap = 0;
+  }
+  const size_t cap = align_up(std::max<size_t>(need, 1 << 20), 1 << 20);
+  if (cudaMalloc(&c->rws, cap) != cudaSuccess) {
+    cudaGetLastError();
+    return HD_ERR_NOMEM;
+  }
+  c->rws_cap = cap;
+  return HD_OK;
+}
+
+// Argument checks shared by the reconstruction entry points; n receives the
+// grid size.
+static int check_lorenzo(const hd_lorenzo* L, uint64_t* n) {
+  if (!L || L->ndim < 1 || L->ndim > 3) return HD_ERR_ARG;
+  if (L->radius < 1 || L->radius > 32768) return HD_ERR_ARG;
+  if (!(L->eb >= 0.0) || !std::isfinite(L->eb)) return HD_ERR_ARG;
+  if (!std::isfinite(static_cast<float>(2.0 * L->eb))) return HD_ERR_ARG;
+  uint64_t m = 1;
+  for (uint32_t k = 0; k < L->ndim; ++k) {
+    const uint64_t e = L->dims[k];
+    if (e && m > (1ull << 48) / e) return HD_ERR_ARG;
+    m *= e;
+  }
+  if (L->n_out > m || (L->n_out && (!L->out_idx || !L->out_val))) return HD_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(L->out_idx) & 7u) || (reinterpret_cast<uintptr_t>(L->out_val) & 3u))
+    return HD_ERR_ARG;
+  *n = m;
+  return HD_OK;
+}
+
+// Decode + 1D reconstruction of one gap-array field in the decoder's kernels.
+static int decompress_fused_1d(hd_ctx* c, const hd_field* f, const hd_lorenzo* L, float* d_out,
+                               void* stream) {
+  c->err_count = 0;
+  c->recon_active = false;
+  c->host_status = HD_ERR_ARG;
+  uint64_t n = 0;
+  int rc = check_lorenzo(L, &n);
+  if (rc) return rc;
+  if (n && (!d_out || (reinterpret_cast<uintptr_t>(d_out) & 15u))) return HD_ERR_ARG;
+  rc = check_field(f, true, d_out);
+  if (rc == HD_PENDING) {
+    c->host_status = HD_OK;
+    return HD_OK;
+  }
+  if (rc) {
+    c->host_status = rc;
+    return rc;
+  }
+  if (f->nbits == 0 || f->n == 0) {
+    c->host_status = HD_ERR_CORRUPT;
+    return HD_OK;
+  }
+  hd::LaunchShape s = field_shape(c, f, true);
+  if (s.S % f->subseq_bits) return HD_ERR_ARG;
+  if (ensure_rws(c, 256) != HD_OK) {
+    c->host_status = HD_ERR_NOMEM;
+    return HD_ERR_NOMEM;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(c->rws, 0, 4, st) != cudaSuccess) {
+    cudaGetLastError();
+    c->host_status = HD_ERR_CUDA;
+    return HD_ERR_CUDA;
+  }
+  std::vector<FieldDesc> descs(1);
+  fill_desc(descs[0], f, s, nullptr);
+  ValueArgs va{d_out, static_cast<int32_t>(L->radius), static_cast<float>(2.0 * L->eb),
+               L->out_idx, L->out_val, L->n_out, reinterpret_cast<uint32_t*>(c->rws)};
+  rc = queue_decode(c, descs, s, false, false, st, &va);
+  c->host_status = rc;
+  if (rc == HD_OK) c->recon_active = true;
+  return rc;
+}
+
 static int reconstruct_locked(hd_ctx* c, const uint16_t* d_codes, const hd_lorenzo* L,
                               float* d_out, void* stream) {
   c->err_count = 0;
@@ -1387,20 +1505,9 @@ static int reconstruct_locked(hd_ctx* c, const uint16_t* d_codes, const hd_loren
     need = align_up(need, 256) + align_up(4ull * zc * P.nb * P.nx, 256) + plane_bytes;
   }
   c->host_status = HD_OK;
-  if (need > c->rws_cap) {
-    if (c->rws) {
-      cudaDeviceSynchronize();
-      cudaFree(c->rws);
-      c->rws = nullptr;
-      c->rws_cap = 0;
-    }
-    const size_t cap = align_up(std::max<size_t>(need, 1 << 20), 1 << 20);
-    if (cudaMalloc(&c->rws, cap) != cudaSuccess) {
-      cudaGetLastError();
-      c->host_status = HD_ERR_NOMEM;
-      return HD_ERR_NOMEM;
-    }
-    c->rws_cap = cap;
+  if (ensure_rws(c, need) != HD_OK) {
+    c->host_status = HD_ERR_NOMEM;
+    return HD_ERR_NOMEM;
   }
   P.err = reinterpret_cast<uint32_t*>(c->rws);
   P.tile_prefix = reinterpret_cast<int32_t*>(c->rws + 256);
@@ -1457,6 +1564,8 @@ int hd_decompress_device(hd_ctx* c, const hd_field* f, const hd_lorenzo* L, floa
   if (L->ndim < 1 || L->ndim > 3 || f->n != n) return HD_ERR_ARG;
   std::lock_guard<std::mutex> lk(c->mu);
   DeviceGuard g(c->device);
+  if (L->ndim == 1 && f->gap && !L->separate && !c->cfg.cr_classes)
+    return decompress_fused_1d(c, f, L, d_out, stream);
   const size_t bytes = align_up(2 * n + 16, 256);
   if (bytes > c->dcodes_cap) {
     if (c->dcodes) {

@@ -132,6 +132,20 @@ struct DecodeParams {
   uint8_t* tile_e;          // self-synchronisation: tile_e[g + 1] = where tile g stopped, minus S
   uint8_t* tile_flag;       // self-synchronisation: 1 = last subsequence overran nbits
   uint8_t* tile_guess;      // self-synchronisation: guessed start offset of each tile
+  // decode + 1D Lorenzo reconstruction of one field (values instead of codes):
+  // k_count also sums each tile's residues, k_scan scans those sums, a tile
+  // kernel adds the outlier corrections, k_write writes float32 values
+  uint32_t* tile_rsum;      // residue sum (code - radius) of each tile, two's complement
+  uint64_t* tile_qbase;     // q before each tile ([units + 1]; the low 32 bits count)
+  uint64_t* tile_obase;     // first outlier at or after each tile's first output ([units + 1])
+  float* vout;              // values [n] (16-byte aligned)
+  int32_t radius;
+  float ebx2;               // float32(2 eb)
+  const uint64_t* out_idx;  // outlier positions, ascending [n_out]
+  const int32_t* out_val;   // outlier residues [n_out]
+  uint64_t n_out;
+  const int32_t* out_corr;  // exclusive prefix of (residue + radius) over the outliers [n_out + 1]
+  uint32_t* verr;           // kErrOutlier
 };
 
 struct PrepParams {

@@ -21,6 +21,8 @@
 // entries and counts into registers while they decode the current tile.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "decode_common.cuh"
 #include "kernels.h"
@@ -66,6 +68,7 @@ struct TileIn {
   uint32_t gap0, gap1;  // gap entries of this and the next subsequence
   uint32_t count;       // k_write: the subsequence's codeword count
   uint64_t base;        // k_write: the tile's first output index (thread 0)
+  uint64_t qbase, olo, ohi;  // k_write values: q before the tile, its outliers (thread 0)
 };
 
 template <int S, int B, bool WRITE>
@@ -79,7 +82,14 @@ __device__ __forceinline__ void fetch_tile(TileIn<S>& in, const DecodeParams& P,
     in.gap1 = (i + 1 < F.nsub) ? __ldg(F.gap + (i + 1) * F.gap_stride) : 0u;
     if (WRITE) in.count = reinterpret_cast<const CT*>(P.counts)[F.count_begin + i];
   }
-  if (WRITE && threadIdx.x == 0) in.base = P.tile_base[g] - P.tile_base[F.unit_begin];
+  if (WRITE && threadIdx.x == 0) {
+    in.base = P.tile_base[g] - P.tile_base[F.unit_begin];
+    if (P.vout) {
+      in.qbase = P.tile_qbase[g];
+      in.olo = P.tile_obase[g];
+      in.ohi = P.tile_obase[g + 1];
+    }
+  }
 }
 
 // Register caps that keep 4 blocks of 256 threads per SM.
@@ -92,13 +102,18 @@ __host__ __device__ constexpr int write_min_blocks() {
   return 1024 / B;
 }
 
-template <int S, int B>
+// E = uint8_t: lengths only (8-bit table).  E = uint16_t / uint32_t: the
+// symbols too (the decode-and-write kernel's table), and each tile's residue
+// sum for decode + reconstruction.
+template <int S, int B, class E>
 __global__ void __launch_bounds__(B, count_min_blocks<B>())
     k_count(const __grid_constant__ DecodeParams P) {
   using CT = typename CountType<S>::T;
+  constexpr bool kSums = sizeof(E) > 1;
+  constexpr Lut kKind = sizeof(E) == 1 ? Lut::k8 : (sizeof(E) == 2 ? Lut::k16 : Lut::k32);
   extern __shared__ __align__(16) unsigned char smem[];
-  uint8_t* s_lut = smem;  // length table
-  uint32_t* s_bits = reinterpret_cast<uint32_t*>(smem + lut_bytes(Lut::k8, P.K));
+  unsigned char* s_lut = smem;  // first-level table
+  uint32_t* s_bits = reinterpret_cast<uint32_t*>(smem + lut_bytes(kKind, P.K));
   __shared__ uint64_t s_end[34];
   __shared__ uint32_t s_base[34];
   __shared__ uint32_t s_meta[3];
@@ -130,14 +145,14 @@ __global__ void __launch_bounds__(B, count_min_blocks<B>())
     }
     if (fi != cur_field) {
       __syncthreads();
-      load_table(F.table, P.K, F.alphabet, Lut::k8, s_lut, s_end, s_base, s_meta, B);
+      load_table(F.table, P.K, F.alphabet, kKind, s_lut, s_end, s_base, s_meta, B);
       cur_field = fi;
       __syncthreads();
     }
     const Tables T = make_tables(F, P.K, s_lut, s_end, s_base, s_meta, nullptr, 0);
     const bool table_ok = s_meta[1] == 0;
     const uint64_t tl = g - F.unit_begin;
-    uint32_t c = 0, err = 0;
+    uint32_t c = 0, err = 0, ssum = 0;
     if (table_ok && i < F.nsub) {
       const uint64_t rem = F.nbits - i * S;
       const uint32_t end = rem < S ? static_cast<uint32_t>(rem) : S;
@@ -149,7 +164,13 @@ __global__ void __launch_bounds__(B, count_min_blocks<B>())
       }
       bool bad = false;
       while (p < end) {
-        p += code_len8(T, peek<B>(col, p), bad);
+        if constexpr (kSums) {
+          uint32_t sym;
+          p += code_sym_t<E>(T, peek<B>(col, p), sym, bad);
+          ssum += sym;
+        } else {
+          p += code_len8(T, peek<B>(col, p), bad);
+        }
         ++c;
       }
       if (bad) err |= kErrCode;
@@ -160,6 +181,10 @@ __global__ void __launch_bounds__(B, count_min_blocks<B>())
     if (t == 0 && !table_ok && tl == 0) atomicOr(F.err, kErrTable);
     const uint32_t C = block_sum<B>(c, s_warp);
     if (t == 0) P.tile_total[g] = C;
+    if constexpr (kSums) {
+      const uint32_t Ssum = block_sum<B>(ssum, s_warp);
+      if (t == 0) P.tile_rsum[g] = Ssum - C * static_cast<uint32_t>(P.radius);
+    }
   }
 }
 
@@ -169,9 +194,34 @@ __global__ void __launch_bounds__(B, count_min_blocks<B>())
 __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ DecodeParams P) {
   const LaunchSize LS = launch_size(P);
   scan_totals(P.tile_total, P.tile_base, LS.lo, LS.units, P.scan_end);
+  if (P.tile_rsum) {
+    __syncthreads();
+    scan_totals(P.tile_rsum, P.tile_qbase, LS.lo, LS.units, nullptr);
+  }
 }
 
-template <int S, int B, class E>
+// Decode + reconstruction: each tile's first outlier, and the outliers'
+// corrections (stored residue + radius for each code 0 counted as -radius)
+// added to the q before the tile (g up to the launch's end).
+__global__ void k_tile_outliers(const __grid_constant__ DecodeParams P) {
+  const LaunchSize LS = launch_size(P);
+  for (uint64_t g = LS.lo + blockIdx.x * 256ull + threadIdx.x; g <= LS.units;
+       g += static_cast<uint64_t>(gridDim.x) * 256) {
+    const uint64_t at = P.tile_base[g];
+    uint64_t lo = 0, hi = P.n_out;
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi) >> 1;
+      if (P.out_idx[mid] < at)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    P.tile_obase[g] = lo;
+    P.tile_qbase[g] += static_cast<uint32_t>(P.out_corr[lo]);
+  }
+}
+
+template <int S, int B, class E, bool VALUES>
 __global__ void __launch_bounds__(B, write_min_blocks<B>())
     k_write(const __grid_constant__ DecodeParams P) {
   constexpr int W = S / 32 + 1;
@@ -187,6 +237,8 @@ __global__ void __launch_bounds__(B, write_min_blocks<B>())
   __shared__ uint32_t s_warp[B / 32];
   __shared__ uint64_t s_tile_base;
   __shared__ uint32_t s_flush_end;
+  __shared__ uint64_t s_vtile[3];  // values: q before the tile, its outlier range
+  __shared__ int32_t s_vw[2 * 32];
 
   const int t = threadIdx.x;
   uint32_t* col = s_bits + t;
@@ -210,7 +262,14 @@ __global__ void __launch_bounds__(B, write_min_blocks<B>())
     const uint64_t i = (g - F.unit_begin) * B + t;
     if (i < F.nsub) put_units<S>(col, nxt.bits, B);
     const uint32_t gap0 = nxt.gap0, count0 = nxt.count;
-    if (t == 0) s_tile_base = nxt.base;
+    if (t == 0) {
+      s_tile_base = nxt.base;
+      if (VALUES) {
+        s_vtile[0] = nxt.qbase;
+        s_vtile[1] = nxt.olo;
+        s_vtile[2] = nxt.ohi;
+      }
+    }
     const uint64_t un = u + gridDim.x;
     if (un < LS.units) {
       g_next = tile_of(un);
@@ -237,8 +296,7 @@ __global__ void __launch_bounds__(B, write_min_blocks<B>())
     const uint32_t o = block_excl_scan<B>(c, s_warp, &C);
     const uint64_t base = s_tile_base;
     if (t == 0 && tl + 1 == F.nunits && base + C != F.n) atomicOr(F.err, kErrCount);
-    window_write<B>(s_out, &s_flush_end, P.window, o, c, C, base, F.out, F.n,
-                    [&](uint16_t* dst) {
+    auto decode = [&](uint16_t* dst) {
                       uint32_t p = gp;
                       bool bad = false;
                       uint32_t j = 0;
@@ -255,7 +313,13 @@ __global__ void __launch_bounds__(B, write_min_blocks<B>())
                         dst[j] = static_cast<uint16_t>(s0);
                       }
                       if (bad) atomicOr(F.err, kErrCode);
-                    });
+                    };
+    if (VALUES)
+      window_write_values<B>(s_out, &s_flush_end, P.window, o, c, C, base, F.n, P,
+                             static_cast<int32_t>(static_cast<uint32_t>(s_vtile[0])),
+                             s_vtile[1], s_vtile[2], s_vw, decode);
+    else
+      window_write<B>(s_out, &s_flush_end, P.window, o, c, C, base, F.out, F.n, decode);
   }
 }
 
@@ -300,21 +364,60 @@ cudaError_t launch_scan(const DecodeParams& p, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
-template <int S, int B>
+template <int S, int B, bool VALUES = false>
 cudaError_t launch_write_sb(const DecodeParams& p, const LaunchShape& s, int num_sms,
                             cudaStream_t stream) {
   if (s.lut16)
-    return launch_persistent(k_write<S, B, uint16_t>, p, B, two_phase_smem_bytes(s), num_sms,
-                             s.grid, stream);
-  return launch_persistent(k_write<S, B, uint32_t>, p, B, two_phase_smem_bytes(s), num_sms,
-                           s.grid, stream);
+    return launch_persistent(k_write<S, B, uint16_t, VALUES>, p, B, two_phase_smem_bytes(s),
+                             num_sms, s.grid, stream);
+  return launch_persistent(k_write<S, B, uint32_t, VALUES>, p, B, two_phase_smem_bytes(s),
+                           num_sms, s.grid, stream);
+}
+
+size_t count_values_smem_bytes(const LaunchShape& s) {
+  const size_t W = s.S / 32 + 1;
+  const size_t b =
+      dev::lut_bytes(s.lut16 ? dev::Lut::k16 : dev::Lut::k32, s.K) + W * s.threads * 4;
+  return (b + 15) & ~static_cast<size_t>(15);
+}
+
+// Decode + reconstruction: counts and residue sums, the two scans, the
+// outlier corrections, then values.
+template <int S, int B>
+cudaError_t launch_values_sb(const DecodeParams& p, const LaunchShape& s, int num_sms,
+                             cudaStream_t stream) {
+  cudaError_t e =
+      s.lut16 ? launch_persistent(k_count<S, B, uint16_t>, p, B, count_values_smem_bytes(s),
+                                  num_sms, s.grid, stream)
+              : launch_persistent(k_count<S, B, uint32_t>, p, B, count_values_smem_bytes(s),
+                                  num_sms, s.grid, stream);
+  if (e != cudaSuccess) return e;
+  e = launch_scan(p, stream);
+  if (e != cudaSuccess) return e;
+  const uint64_t units = p.unit_hi ? p.unit_hi : p.total_units;
+  const uint64_t blocks = std::min<uint64_t>((units - p.unit_lo + 1 + 255) / 256, 4096);
+  k_tile_outliers<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(p);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_write_sb<S, B, true>(p, s, num_sms, stream);
+}
+
+template <int S>
+cudaError_t launch_values_s(const DecodeParams& p, const LaunchShape& s, int num_sms,
+                            cudaStream_t stream) {
+  switch (s.threads) {
+    case 128: return launch_values_sb<S, 128>(p, s, num_sms, stream);
+    case 256: return launch_values_sb<S, 256>(p, s, num_sms, stream);
+    case 512: return launch_values_sb<S, 512>(p, s, num_sms, stream);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <int S, int B>
 cudaError_t launch_sb(const DecodeParams& p, const LaunchShape& s, int num_sms,
                       cudaStream_t stream) {
-  cudaError_t e =
-      launch_persistent(k_count<S, B>, p, B, count_smem_bytes(s), num_sms, s.grid, stream);
+  cudaError_t e = launch_persistent(k_count<S, B, uint8_t>, p, B, count_smem_bytes(s), num_sms,
+                                    s.grid, stream);
   if (e != cudaSuccess) return e;
   e = launch_scan(p, stream);
   if (e != cudaSuccess) return e;
@@ -375,13 +478,27 @@ cudaError_t launch_decode_two_phase(const DecodeParams& p, const LaunchShape& s,
   }
 }
 
+cudaError_t launch_decode_values(const DecodeParams& p, const LaunchShape& s, int num_sms,
+                                 cudaStream_t stream) {
+  if (p.long_cap != s.long_cap || p.window != s.window || s.window < s.S) return cudaErrorInvalidValue;
+  if (!p.vout || !p.tile_rsum || !p.tile_qbase || !p.tile_obase || !p.out_corr)
+    return cudaErrorInvalidValue;
+  switch (s.S) {
+    case 64: return launch_values_s<64>(p, s, num_sms, stream);
+    case 128: return launch_values_s<128>(p, s, num_sms, stream);
+    case 256: return launch_values_s<256>(p, s, num_sms, stream);
+    case 512: return launch_values_s<512>(p, s, num_sms, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int S>
 cudaError_t launch_count_s(const DecodeParams& p, const LaunchShape& s, int num_sms,
                            cudaStream_t stream) {
   switch (s.threads) {
-    case 128: return launch_persistent(k_count<S, 128>, p, 128, count_smem_bytes(s), num_sms, s.grid, stream);
-    case 256: return launch_persistent(k_count<S, 256>, p, 256, count_smem_bytes(s), num_sms, s.grid, stream);
-    case 512: return launch_persistent(k_count<S, 512>, p, 512, count_smem_bytes(s), num_sms, s.grid, stream);
+    case 128: return launch_persistent(k_count<S, 128, uint8_t>, p, 128, count_smem_bytes(s), num_sms, s.grid, stream);
+    case 256: return launch_persistent(k_count<S, 256, uint8_t>, p, 256, count_smem_bytes(s), num_sms, s.grid, stream);
+    case 512: return launch_persistent(k_count<S, 512, uint8_t>, p, 512, count_smem_bytes(s), num_sms, s.grid, stream);
     default: return cudaErrorInvalidValue;
   }
 }

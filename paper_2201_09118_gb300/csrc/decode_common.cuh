@@ -279,6 +279,152 @@ __device__ __forceinline__ void window_write(uint16_t* s_out, uint32_t* s_flush_
   }
 }
 
+// True when a 32-bit word may hold a zero half-word (exact for the high half;
+// a zero low half's borrow can make it fire for the high one too).
+__device__ __forceinline__ bool has_zero_half(uint32_t w) {
+  return ((w - 0x00010001u) & ~w & 0x80008000u) != 0;
+}
+
+// Decode + 1D Lorenzo reconstruction: the residue of code c at output G (code
+// 0: the outlier stored for G, searched in the tile's outliers [olo, ohi)).
+__device__ __forceinline__ int32_t value_residue(const DecodeParams& P, uint32_t c, uint64_t G,
+                                                 uint64_t olo, uint64_t ohi) {
+  if (c) return static_cast<int32_t>(c) - P.radius;
+  uint64_t lo = olo, hi = ohi;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (P.out_idx[mid] < G)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  if (lo < ohi && P.out_idx[lo] == G) return P.out_val[lo];
+  atomicOr(P.verr, kErrOutlier);
+  return 0;
+}
+
+// Writes the values of outputs [G0, G1): q is `carry` plus the inclusive
+// prefix of the residues; value = float32(q) * float32(2 eb).  Positions are
+// taken relative to A = G0 rounded down to a multiple of 4; the code of
+// position x sits at s_pos[x] (s_pos 16-byte aligned, x from G0 - A), so a
+// thread's 8 consecutive positions are one 16-byte shared load and two
+// 16-byte global stores.  B * 8 positions per row, one barrier per row (warp
+// totals double-buffered in s_vw[2][32], scanned with shuffles).  carry
+// leaves with q at G1 - 1.
+template <int B>
+__device__ __forceinline__ void flush_values(const uint16_t* s_pos, uint64_t G0, uint64_t G1,
+                                             uint64_t n, int32_t& carry, const DecodeParams& P,
+                                             uint64_t olo, uint64_t ohi, int32_t* s_vw) {
+  constexpr int NW = B / 32;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const uint64_t A = G0 & ~3ull;
+  const uint32_t lo = static_cast<uint32_t>(G0 - A);       // first valid position
+  const uint32_t hi = lo + static_cast<uint32_t>(G1 - G0);  // end of the valid positions
+  const uint64_t room = n > A ? n - A : 0ull;
+  const uint32_t hn = room < hi ? static_cast<uint32_t>(room) : hi;  // end of the stored ones
+  int buf = 0;
+  for (uint32_t x0 = 0; x0 < hi; x0 += 8u * B, buf ^= 1) {
+    const uint32_t x = x0 + 8u * t;
+    int32_t r[8];
+    if (x >= lo && x + 8 <= hi) {
+      const uint4 u = *reinterpret_cast<const uint4*>(s_pos + x);
+      const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+      if (has_zero_half(u.x) | has_zero_half(u.y) | has_zero_half(u.z) | has_zero_half(u.w)) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          r[k] = value_residue(P, (w[k >> 1] >> (16 * (k & 1))) & 0xffffu, A + x + k, olo, ohi);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          r[k] = static_cast<int32_t>((w[k >> 1] >> (16 * (k & 1))) & 0xffffu) - P.radius;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t xk = x + k;
+        r[k] = xk >= lo && xk < hi ? value_residue(P, s_pos[xk], A + xk, olo, ohi) : 0;
+      }
+    }
+#pragma unroll
+    for (int k = 1; k < 8; ++k) r[k] += r[k - 1];
+    int32_t incl = r[7];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    int32_t* sw = s_vw + buf * 32;
+    if (lane == 31) sw[warp] = incl;
+    __syncthreads();
+    // warp totals of the row, scanned by every warp with shuffles
+    const int32_t wt = lane < NW ? sw[lane] : 0;
+    int32_t wi = wt;
+#pragma unroll
+    for (int o = 1; o < NW; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    const int32_t before = __shfl_sync(0xffffffffu, wi - wt, warp);
+    const int32_t row = __shfl_sync(0xffffffffu, wi, NW - 1);
+    const int32_t e = carry + before + incl - r[7];
+    carry += row;
+    if (x < hi) {
+      float f[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) f[k] = __fmul_rn(__int2float_rn(e + r[k]), P.ebx2);
+      float* dst = P.vout + A + x;
+      if (x >= lo && x + 8 <= hn) {
+        __stcs(reinterpret_cast<float4*>(dst), make_float4(f[0], f[1], f[2], f[3]));
+        __stcs(reinterpret_cast<float4*>(dst) + 1, make_float4(f[4], f[5], f[6], f[7]));
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (x + k >= lo && x + k < hn) dst[k] = f[k];
+      }
+    }
+  }
+}
+
+// Algorithm 1's window (as window_write) with float32 values out: each pass's
+// codes are decoded into s_out[G & 3 ..) (the window holds window + 16 codes)
+// and written by flush_values, q running on from the tile's prefix q0 across
+// passes.  s_out is 16-byte aligned.
+template <int B, class DecodeFn>
+__device__ __forceinline__ void window_write_values(uint16_t* s_out, uint32_t* s_flush_end,
+                                                    uint32_t window, uint32_t o, uint32_t c,
+                                                    uint32_t C, uint64_t base, uint64_t n,
+                                                    const DecodeParams& P, int32_t q0,
+                                                    uint64_t olo, uint64_t ohi, int32_t* s_vw,
+                                                    DecodeFn&& decode) {
+  const int t = threadIdx.x;
+  int32_t carry = q0;
+  if (C <= window) {
+    if (c) decode(s_out + (base & 3u) + o);
+    __syncthreads();
+    flush_values<B>(s_out, base, base + C, n, carry, P, olo, ohi, s_vw);
+    __syncthreads();
+    return;
+  }
+  bool done = c == 0;
+  uint32_t ws = 0;
+  while (ws < C) {
+    const uint32_t we = ws + window;
+    if (t == 0) *s_flush_end = C < we ? C : we;
+    __syncthreads();
+    if (!done && o < we && o + c > we) atomicMin(s_flush_end, o);
+    __syncthreads();
+    const uint32_t fe = *s_flush_end;
+    if (!done && o + c <= fe) {
+      decode(s_out + ((base + ws) & 3u) + (o - ws));
+      done = true;
+    }
+    __syncthreads();
+    flush_values<B>(s_out, base + ws, base + fe, n, carry, P, olo, ohi, s_vw);
+    __syncthreads();
+    ws = fe;
+  }
+}
+
 // Which first-level table a kernel keeps in shared memory.
 enum class Lut { k32, k16, k8 };
 

@@ -57,6 +57,14 @@ cudaError_t launch_phase(const DecodeParams& p, const LaunchShape& s, Phase phas
 cudaError_t launch_classify(const DecodeParams& p, uint32_t unit, uint32_t nclass,
                             uint32_t* counts, uint32_t* lists, uint64_t cap, cudaStream_t stream);
 
+// Decode + 1D Lorenzo reconstruction of one gap-array field (float32 values
+// to p.vout instead of codes): the count kernel also sums each tile's
+// residues (symbol tables), the tile scan scans both, a kernel adds each
+// tile's outlier corrections (p.out_corr: exclusive prefix of residue +
+// radius over the outliers) and the decode-and-write kernel writes values.
+cudaError_t launch_decode_values(const DecodeParams& p, const LaunchShape& s, int num_sms,
+                                 cudaStream_t stream);
+
 // Tile scan and decode-and-write kernel, for fields whose counts and gap
 // entries are already in place (self-synchronisation writes them).
 cudaError_t launch_write(const DecodeParams& p, const LaunchShape& s, int num_sms,
@@ -103,6 +111,9 @@ cudaError_t launch_lorenzo_slices(const LorenzoParams& p, int num_sms, cudaStrea
 // z kernel; used when lorenzo_slice_path(nx, nz, num_sms).  Needs no band or
 // plane buffers (one launch covers all slices).
 bool lorenzo_slice_path(uint64_t nx, uint64_t nz, int num_sms);
+// corr[k] = sum over outliers j < k of (val[j] + radius), k = 0 .. n_out.
+cudaError_t launch_outlier_prefix(const int32_t* val, uint64_t n_out, int32_t radius,
+                                  int32_t* corr, cudaStream_t stream);
 cudaError_t launch_lorenzo_whole_slices(const LorenzoParams& p, int num_sms, cudaStream_t stream);
 
 }  // namespace hd

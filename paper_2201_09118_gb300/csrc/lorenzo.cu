@@ -164,6 +164,29 @@ __global__ void __launch_bounds__(k1ScanThreads) k_lorenzo_1d_scan(int32_t* a, u
   }
 }
 
+// Exclusive prefix of (residue + radius) over the outlier list (one block):
+// the correction of q for the outliers before a position, whose codes 0 a
+// residue sum over codes counts as -radius.
+__global__ void __launch_bounds__(k1ScanThreads) k_outlier_prefix(const int32_t* val, uint64_t n,
+                                                                  int32_t radius, int32_t* corr) {
+  __shared__ int32_t s_w[k1ScanThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const uint64_t per = (n + k1ScanThreads - 1) / k1ScanThreads;
+  const uint64_t lo = min(n, per * t), hi = min(n, lo + per);
+  int32_t sum = 0;
+  for (uint64_t k = lo; k < hi; ++k) sum += val[k] + radius;
+  const int32_t incl = warp_incl(sum, lane);
+  if (lane == 31) s_w[w] = incl;
+  __syncthreads();
+  int32_t run = incl - sum;
+  for (int k = 0; k < w; ++k) run += s_w[k];
+  for (uint64_t k = lo; k < hi; ++k) {
+    corr[k] = run;
+    run += val[k] + radius;
+  }
+  if (t == k1ScanThreads - 1) corr[n] = run;
+}
+
 // Reconstruction of one tile from its prefix.
 __global__ void __launch_bounds__(kThreads) k_lorenzo_1d(LorenzoParams P) {
   __shared__ int32_t s_warp[k1Rows][kWarps];
@@ -667,6 +690,12 @@ uint32_t lorenzo_rows_per_band(uint64_t nx) {
 
 size_t lorenzo_band_smem(uint32_t yb, uint64_t nx) {
   return nx <= kWarpBandMaxRow ? 0 : 4ull * yb * nx;
+}
+
+cudaError_t launch_outlier_prefix(const int32_t* val, uint64_t n_out, int32_t radius,
+                                  int32_t* corr, cudaStream_t st) {
+  k_outlier_prefix<<<1, k1ScanThreads, 0, st>>>(val, n_out, radius, corr);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_lorenzo_1d(const LorenzoParams& P, int num_sms, cudaStream_t st) {

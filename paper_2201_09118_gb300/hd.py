@@ -80,11 +80,12 @@ class hd_lorenzo(ctypes.Structure):
                 ("dims", ctypes.c_uint64 * 3), ("eb", ctypes.c_double),
                 ("out_idx", ctypes.c_void_p), ("out_val", ctypes.c_void_p),
                 ("n_out", ctypes.c_uint64), ("chunk_slices", ctypes.c_uint32),
-                ("band_rows", ctypes.c_uint32)]
+                ("band_rows", ctypes.c_uint32), ("separate", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32)]
 
 
 def lorenzo_params(dims, radius: int, eb: float, out_idx=None, out_val=None,
-                   chunk_slices: int = 0, band_rows: int = 0) -> hd_lorenzo:
+                   chunk_slices: int = 0, band_rows: int = 0, separate: bool = False) -> hd_lorenzo:
     """hd_lorenzo for a grid (dims[0] fastest) and device outlier tensors."""
     L = hd_lorenzo()
     L.ndim = len(dims)
@@ -98,6 +99,7 @@ def lorenzo_params(dims, radius: int, eb: float, out_idx=None, out_val=None,
     L.n_out = n_out
     L.chunk_slices = int(chunk_slices)
     L.band_rows = int(band_rows)
+    L.separate = 1 if separate else 0
     return L
 
 

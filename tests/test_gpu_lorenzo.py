@@ -208,3 +208,108 @@ def test_decompress_512_cube(ctx):
     assert same_bits(got, want)
     fl = g["field"].reshape(-1).astype(np.float64)
     assert np.all(np.abs(got - fl) <= g["eb"] * (1 + 1e-6) + 2.0 ** -23 * np.abs(fl))
+
+
+def _compressed_1d(n, rel_eb, radius, seed):
+    g = quantized((n,), rel_eb=rel_eb, radius=radius, seed=seed, noise=1e-4)
+    c = oracle.compress(g["codes"], 2 * radius, S=128)
+    return g, c
+
+
+@pytest.mark.parametrize("n,rel_eb,radius", [(1, 1e-3, 64), (7, 1e-3, 64), (5000, 1e-4, 16),
+                                             ((1 << 20) + 3, 1e-4, 512),
+                                             ((1 << 22) + 1, 1e-6, 2048)])
+def test_fused_1d_equals_oracle_and_separate(ctx, n, rel_eb, radius):
+    """1D gap-array fields decode straight into values (no codes in HBM);
+    bit for bit the oracle's reconstruction of the oracle's decode, and the
+    same as decode-then-reconstruct."""
+    from paper_2201_09118_gb300 import hd
+    g, c = _compressed_1d(n, rel_eb, radius, seed=n % 101)
+    dec = oracle.decode(c["words"], c["nbits"], c["codes"], c["lengths"], n_cap=c["n"])
+    want = olz.reconstruct(dec, (n,), radius, g["eb"], g["out_idx"], g["out_val"])
+    _, idx, val = to_dev(g)
+    f = _device_field(c)
+    outs = []
+    for separate in (False, True):
+        out = torch.full((n + 8,), float("nan"), dtype=torch.float32, device="cuda")
+        ctx.decompress(f, hd.lorenzo_params((n,), radius, g["eb"], idx, val, separate=separate),
+                       out)
+        assert ctx.status() == 0
+        r = out.cpu().numpy()
+        assert np.all(np.isnan(r[n:]))
+        outs.append(r[:n])
+    assert same_bits(outs[0], want)
+    assert same_bits(outs[1], want)
+
+
+def test_fused_1d_several_window_passes(ctx):
+    # a small output window forces several passes per tile (q carried across)
+    from paper_2201_09118_gb300 import hd
+    n = 300_001
+    g, c = _compressed_1d(n, 1e-2, 64, seed=3)  # ~1-2 bits per code: crowded tiles
+    want = olz.reconstruct(g["codes"], (n,), 64, g["eb"], g["out_idx"], g["out_val"])
+    _, idx, val = to_dev(g)
+    f = _device_field(c)
+    try:
+        ctx.set_config(subseq_bits=256, threads=256, window=1024)
+        out = torch.empty(n, dtype=torch.float32, device="cuda")
+        ctx.decompress(f, hd.lorenzo_params((n,), 64, g["eb"], idx, val), out)
+        assert ctx.status() == 0
+        assert same_bits(out.cpu().numpy(), want)
+    finally:
+        ctx.reset_config()
+
+
+def test_fused_1d_heavy_outliers_and_large_q(ctx):
+    from paper_2201_09118_gb300 import hd
+    n = 200_000
+    rng = np.random.default_rng(9)
+    codes = rng.integers(1, 16, n).astype(np.uint16)
+    out_idx = np.sort(rng.choice(n, size=n // 5, replace=False)).astype(np.uint64)
+    codes[out_idx.astype(np.int64)] = 0
+    out_val = rng.integers(-3000, 3000, out_idx.size).astype(np.int32)
+    out_val[0] = (1 << 24) + 1
+    g = {"codes": codes, "eb": 0.05, "out_idx": out_idx, "out_val": out_val}
+    c = oracle.compress(codes, 16, S=128)
+    want = olz.reconstruct(codes, (n,), 8, 0.05, out_idx, out_val)
+    _, idx, val = to_dev(g)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    ctx.decompress(_device_field(c), hd.lorenzo_params((n,), 8, 0.05, idx, val), out)
+    assert ctx.status() == 0
+    assert same_bits(out.cpu().numpy(), want)
+
+
+def test_fused_1d_missing_outlier_and_corrupt_stream(ctx):
+    from paper_2201_09118_gb300 import hd
+    n = 50_000
+    codes = np.full(n, 512, np.uint16)
+    codes[[10, 40_000]] = 0
+    c = oracle.compress(codes, 1024, S=128)
+    f = _device_field(c)
+    out = torch.full((n + 8,), float("nan"), dtype=torch.float32, device="cuda")
+    idx = torch.tensor([10], dtype=torch.int64, device="cuda")
+    val = torch.tensor([5], dtype=torch.int32, device="cuda")
+    ctx.decompress(f, hd.lorenzo_params((n,), 512, 1.0, idx, val), out)
+    assert ctx.status() == hd.HD_ERR_CORRUPT  # position 40,000 has no stored residue
+    # a stream claiming one symbol more than it holds: corrupt, nothing past n
+    bad = hd.DeviceField(f.words, f.nbits, f.gap, f.subseq_bits, f.lengths, f.alphabet, n + 1)
+    out2 = torch.full((n + 9,), float("nan"), dtype=torch.float32, device="cuda")
+    idx2 = torch.tensor([10, 40_000], dtype=torch.int64, device="cuda")
+    val2 = torch.tensor([5, 6], dtype=torch.int32, device="cuda")
+    ctx.decompress(bad, hd.lorenzo_params((n + 1,), 512, 1.0, idx2, val2), out2)
+    assert ctx.status() == hd.HD_ERR_CORRUPT
+    assert np.all(np.isnan(out2.cpu().numpy()[n + 1:]))
+
+
+def test_fused_1d_hacc_size(ctx):
+    """280,953,867 codes (the HACC particle count), rel. error bound 1e-4:
+    fused decode + reconstruction against the oracle's reconstruction."""
+    from paper_2201_09118_gb300 import hd
+    n = 280_953_867
+    g, c = _compressed_1d(n, 1e-4, 512, seed=1002)
+    want = olz.reconstruct(g["codes"], (n,), 512, g["eb"], g["out_idx"], g["out_val"])
+    _, idx, val = to_dev(g)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    ctx.decompress(_device_field(c), hd.lorenzo_params((n,), 512, g["eb"], idx, val), out)
+    assert ctx.status() == 0
+    assert same_bits(out.cpu().numpy(), want)
