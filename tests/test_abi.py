@@ -91,3 +91,29 @@ def test_codebook_from_counts_matches_codebook_from_symbols():
     assert np.array_equal(hd.hd_build_codebook_freq(freq, 32), hd.hd_build_codebook(x, 1024, 32))
     with pytest.raises(hd.HDError):
         hd.hd_build_codebook_freq(np.zeros(1, np.uint64), 32)  # alphabet < 2
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ABI struct the binding declares has the header's size and field
+    offsets (compiled from include/hd.h with the host C compiler)."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    exe = str(tmp_path / "abi_layout")
+    subprocess.run([cc, "-O0", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "native", "abi_layout.c"), "-o", exe], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    got = dict(line.rsplit(" ", 1) for line in out.strip().splitlines())
+    from paper_2201_09118_gb300 import hd
+    for name, cls in [("hd_stream_info", hd.hd_stream_info), ("hd_field", hd.hd_field),
+                      ("hd_config", hd.hd_config), ("hd_serve_config", hd.hd_serve_config),
+                      ("hd_result", hd.hd_result), ("hd_serve_stats_t", hd.hd_serve_stats_t),
+                      ("hd_lorenzo", hd.hd_lorenzo)]:
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            key = f"{name}.{field}"
+            if key in got:
+                assert int(got[key]) == getattr(cls, field).offset, key

@@ -313,3 +313,27 @@ def test_fused_1d_hacc_size(ctx):
     ctx.decompress(_device_field(c), hd.lorenzo_params((n,), 512, g["eb"], idx, val), out)
     assert ctx.status() == 0
     assert same_bits(out.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("mode", ["selfsync", "cr_classes", "tuned"])
+def test_1d_decompress_other_paths(ctx, mode):
+    """1D decompression when the fused path does not apply (self-synchronised
+    field, CR-class launches) or runs in an autotuned shape."""
+    from paper_2201_09118_gb300 import hd
+    n = 400_003
+    g, c = _compressed_1d(n, 1e-4, 512, seed=77)
+    want = olz.reconstruct(g["codes"], (n,), 512, g["eb"], g["out_idx"], g["out_val"])
+    enc = {"words": c["words"], "gap": c["gap"], "nbits": c["nbits"], "subseq_bits": c["S"]}
+    f = hd.DeviceField.upload(enc, c["lengths"], c["n"], with_gap=mode != "selfsync")
+    _, idx, val = to_dev(g)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    try:
+        if mode == "cr_classes":
+            ctx.set_config(cr_classes=4)
+        if mode == "tuned":
+            ctx.autotune([f], [torch.empty(n, dtype=torch.int16, device="cuda")])
+        ctx.decompress(f, hd.lorenzo_params((n,), 512, g["eb"], idx, val), out)
+        assert ctx.status() == 0
+        assert same_bits(out.cpu().numpy(), want)
+    finally:
+        ctx.reset_config()
