@@ -368,7 +368,7 @@ def run_decompress_1d(hd, torch, ctx_dev, stream, flush, steps: int = 5, n: int 
     vals = torch.empty(n, dtype=torch.float32, device=dev)
     dec = torch.empty(n, dtype=torch.int16, device=dev)
     ctx = hd.Context(ctx_dev)
-    ctx.autotune([f], [dec], stream)
+    launch = ctx.autotune([f], [dec], stream)
 
     def timed(fn):
         fn()
@@ -400,7 +400,7 @@ def run_decompress_1d(hd, torch, ctx_dev, stream, flush, steps: int = 5, n: int 
             "value": 4.0 * n / (fused * 1e-3) / 1e9,
             "unit": "GB/s (float32 values out, fused decode + reconstruction)",
             "fused_ms": fused, "separate_ms": separate, "decode_ms": decode,
-            "reconstruct_ms": recon, "status_ok": bool(ok)}
+            "reconstruct_ms": recon, "launch": launch, "status_ok": bool(ok)}
 
 
 def mixed_cr_workload(n_seg: int = 32, seg: int = 1 << 21, seed: int = 1005):
@@ -781,6 +781,43 @@ def run_profile_recon(args):
     return 0 if st == 0 else 1
 
 
+def run_profile_fused1d(args, n: int = 280_953_867):
+    """Fused decode + reconstruction of the 1D field of the decompress_1d leg,
+    `steps` times after `warmup` (profiler captures); one timing line."""
+    import synth
+    import torch
+    from paper_2201_09118_gb300 import hd
+    torch.cuda.set_device(0)
+    f1 = synth.fourier_field((n,), noise=1e-4, kmax=8, seed=1002)
+    g = synth.lorenzo_quantize(f1, 1e-4, radius=512)
+    del f1
+    lengths = hd.hd_build_codebook(g["codes"], 1024, 32)
+    enc = hd.hd_encode(g["codes"], lengths, 128)
+    f = hd.DeviceField.upload(enc, lengths, n)
+    idx = torch.from_numpy(g["out_idx"].view(np.int64)).cuda()
+    val = torch.from_numpy(g["out_val"]).cuda()
+    vals = torch.empty(n, dtype=torch.float32, device="cuda")
+    ctx = hd.Context(0)
+    if args.threads or args.window or args.lut_bits or args.subseq_bits:
+        ctx.set_config(subseq_bits=args.subseq_bits, threads=args.threads, window=args.window,
+                       lut_bits=args.lut_bits)
+    L = hd.lorenzo_params((n,), 512, g["eb"], idx, val)
+    for _ in range(args.warmup):
+        ctx.decompress(f, L, vals)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        ctx.decompress(f, L, vals)
+    b.record()
+    b.synchronize()
+    st = ctx.status()
+    print(json.dumps({"profile_case": "fused1d", "n_codes": n,
+                      "ms": a.elapsed_time(b) / max(1, args.steps), "ok": st == 0}), flush=True)
+    return 0 if st == 0 else 1
+
+
 def run_profile_case(args):
     """Decodes one strategy `steps` times after `warmup` (for profiler
     captures); prints one timing line, no bench line."""
@@ -788,6 +825,8 @@ def run_profile_case(args):
     from paper_2201_09118_gb300 import hd
     if args.profile_strategy == "recon":
         return run_profile_recon(args)
+    if args.profile_strategy == "fused1d":
+        return run_profile_fused1d(args)
     torch.cuda.set_device(0)
     codes = workload_codes(args.side, seed=1001)
     n = codes.size
@@ -830,7 +869,8 @@ def main():
                     help="skip the batched (256 fields) and served (request trace) legs")
     ap.add_argument("--batch-fields", dest="batch_fields", type=int, default=256)
     ap.add_argument("--requests", type=int, default=10000)
-    ap.add_argument("--profile-strategy", choices=["gap", "selfsync", "recon"], default=None,
+    ap.add_argument("--profile-strategy", choices=["gap", "selfsync", "recon", "fused1d"],
+                    default=None,
                     help="decode one strategy (or reconstruct the decoded codes) only and "
                          "print its time (profiler runs)")
     args = ap.parse_args()
