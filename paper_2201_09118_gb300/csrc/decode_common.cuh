@@ -550,55 +550,66 @@ __device__ __forceinline__ void stage_units(uint32_t* col, const FieldDesc& F, u
 // kScanThreads: base[j] = base[lo] + sum of total[k] for lo <= k < j, for j in
 // [lo, hi], where base[lo] is read as 0 when lo == 0 (a later range continues
 // the previous one).  end_out (may be NULL) also receives base[hi].  The
-// totals are taken in passes of kScanThreads * kScanPer; in a pass each thread
-// owns kScanPer consecutive totals, which it loads at once (independent
-// loads), and a block scan of the per-thread sums gives each run's first base.
+// totals are taken in passes of kScanPer rows of kScanThreads; thread t loads
+// and stores entry t of every row (coalesced), the rows' warp scans run
+// together, warp k scans the warp totals of row k, and each thread adds the
+// rows before its own.  A warp's 32 totals must sum below 2^32 (tile totals
+// are at most 2^18) or be meant modulo 2^32.
 constexpr int kScanThreads = 1024;
 constexpr int kScanPer = 16;
 
 __device__ __forceinline__ void scan_totals(const uint32_t* total, uint64_t* base, uint64_t lo,
                                             uint64_t hi, uint64_t* end_out) {
-  __shared__ uint64_t s_part[kScanThreads / 32];
+  constexpr int NW = kScanThreads / 32;
+  static_assert(kScanPer <= NW, "one warp per row");
+  __shared__ uint64_t s_off[kScanPer][NW];  // per row: exclusive warp offsets
+  __shared__ uint64_t s_row[kScanPer];      // per row: its total
   __shared__ uint64_t s_carry;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   if (t == 0) s_carry = lo ? base[lo] : 0ull;
   __syncthreads();
   for (uint64_t p0 = lo; p0 < hi; p0 += static_cast<uint64_t>(kScanThreads) * kScanPer) {
-    const uint64_t a = p0 + static_cast<uint64_t>(t) * kScanPer;
-    uint32_t v[kScanPer];
-    uint64_t sum = 0;
+    uint32_t v[kScanPer], incl[kScanPer];
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
-      v[k] = a + k < hi ? total[a + k] : 0u;
-      sum += v[k];
+      const uint64_t i = p0 + static_cast<uint64_t>(k) * kScanThreads + t;
+      v[k] = i < hi ? total[i] : 0u;
+      incl[k] = v[k];
     }
-    uint64_t incl = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += u;
+#pragma unroll
+      for (int k = 0; k < kScanPer; ++k) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl[k], o);
+        if (lane >= o) incl[k] += u;
+      }
     }
-    if (lane == 31) s_part[warp] = incl;
+    if (lane == 31) {
+#pragma unroll
+      for (int k = 0; k < kScanPer; ++k) s_off[k][warp] = incl[k];
+    }
     __syncthreads();
-    if (warp == 0) {
-      uint64_t x = s_part[lane];
+    if (warp < kScanPer) {
+      const uint64_t x = s_off[warp][lane];
+      uint64_t xi = x;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t u = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += u;
+        const uint64_t u = __shfl_up_sync(0xffffffffu, xi, o);
+        if (lane >= o) xi += u;
       }
-      s_part[lane] = x;
+      s_off[warp][lane] = xi - x;
+      if (lane == 31) s_row[warp] = xi;
     }
     __syncthreads();
-    uint64_t run = s_carry + (warp ? s_part[warp - 1] : 0ull) + incl - sum;
+    uint64_t run = s_carry;
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
-      if (a + k < hi) base[a + k] = run;
-      run += v[k];
+      const uint64_t i = p0 + static_cast<uint64_t>(k) * kScanThreads + t;
+      if (i < hi) base[i] = run + s_off[k][warp] + (incl[k] - v[k]);
+      run += s_row[k];
     }
-    const uint64_t pass_total = s_part[kScanThreads / 32 - 1];
     __syncthreads();
-    if (t == 0) s_carry += pass_total;
+    if (t == 0) s_carry = run;
     __syncthreads();
   }
   if (t == 0) {
