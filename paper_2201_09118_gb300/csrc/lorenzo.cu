@@ -9,19 +9,23 @@
 //
 // 1D: reduce, scan, reconstruct: residue sums of tiles of 8192 codes, an
 // exclusive scan of the tile sums, and a pass that scans each tile again
-// from its prefix and writes the floats (8 bytes per code moved).
-// 2D/3D: the prefix sums are separable, so per group of slices
-//   k_lorenzo_band      one block per band of yb rows of a slice: residues,
-//                       row sums (x) and the band's column sums (y) in shared
-//                       memory; writes the band as int32 into the output
-//                       buffer and the band's column totals;
+// from its prefix and writes the floats (8 bytes per code moved).  (Decode +
+// reconstruction of 1D fields runs instead inside the decoder's kernels.)
+// 3D with many slices and rows of at most 1024 codes, the slice path:
+//   k_lorenzo_slice     one block per slice: per-warp column sums of residues,
+//                       one barrier, then each warp streams its rows (x prefix
+//                       by lane and warp scans, y sums in registers) from the
+//                       carry of the rows above, writing int32;
+//   k_lorenzo_zscan     the sum along z, float32 values in place of the int32s.
+// Otherwise (2D, few slices, long rows) the band path, per group of slices:
+//   k_lorenzo_warpband  one warp per band of rows in registers (rows up to
+//   / k_lorenzo_band    1024 codes), or one block per band in shared memory:
+//                       x and in-band y prefixes as int32, band column totals;
 //   k_lorenzo_bandscan  exclusive scan of the band totals over the bands of
 //                       each slice (the y carry of every band);
-//   k_lorenzo_zscan     one thread per (y, x): adds the band carry, runs the
-//                       sum along z (carried between groups in `plane`) and
-//                       writes the float32 values in place of the int32s.
-// Groups are sized so that their int32 intermediate stays in L2 between the
-// band and z kernels.
+//   k_lorenzo_zscan     adds the band carry, runs the sum along z (carried
+//                       between groups in `plane`) and writes the float32
+//                       values in place of the int32s.
 #include <cuda_runtime.h>
 
 #include <algorithm>
