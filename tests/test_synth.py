@@ -71,3 +71,21 @@ def test_batch_spec_ranges():
     assert all(1e-6 <= s.rel_eb <= 1e-2 for s in spec)
     # log-uniform: the median size is near the geometric mean of the range
     assert abs(math.log2(float(np.median(ns))) - 21) < 1.0
+
+
+def test_lorenzo_radius_boundary_and_outlier_list():
+    # a 1D field whose residues are exactly +-(R-1) and +-R (eb = 0.5 so that
+    # q = round(x)): |d| < R is coded as d + R, |d| >= R goes to the outlier list
+    R = 8
+    q = np.cumsum([0, R - 1, -(R - 1), R, -R, 3]).astype(np.float64)
+    x = np.concatenate([q, [0.0, float(q.max() - q.min())]])  # fix the range
+    rel = 0.5 / (x.max() - x.min())
+    g = synth.lorenzo_quantize(x, rel, radius=R, keep_q=True)
+    assert np.array_equal(g["q"], np.round(x).astype(np.int64))
+    d = np.diff(np.concatenate([[0], g["q"]]))
+    inl = np.abs(d) < R
+    assert np.array_equal(g["codes"][inl], (d[inl] + R).astype(np.uint16))
+    assert np.all(g["codes"][~inl] == 0)
+    assert np.array_equal(g["out_idx"], np.flatnonzero(~inl).astype(np.uint64))
+    assert np.array_equal(g["out_val"], d[~inl].astype(np.int32))
+    assert g["codes"][1] == 2 * R - 1 and g["codes"][2] == 1
