@@ -403,6 +403,51 @@ def run_decompress_1d(hd, torch, ctx_dev, stream, flush, steps: int = 5, n: int 
             "reconstruct_ms": recon, "launch": launch, "status_ok": bool(ok)}
 
 
+def run_skew(hd, torch, ctx_dev, stream, flush, n: int = 1 << 26, steps: int = 5):
+    """Decode throughput across compressibility: 1D fields (the same smooth
+    generator, 8 Fourier modes to bound generation time) quantized at relative
+    error bounds 1e-2 / 1e-4 / 1e-6 with alphabets 256 / 1024 / 4096, gap
+    array (autotuned shape) and self-synchronisation."""
+    import synth
+    dev = f"cuda:{ctx_dev}"
+    out = torch.empty(n, dtype=torch.int16, device=dev)
+    res = []
+    for rel_eb, alphabet in ((1e-2, 256), (1e-4, 1024), (1e-6, 4096)):
+        f1 = synth.fourier_field((n,), noise=1e-4, kmax=8, seed=1002)
+        codes, _, _ = synth.lorenzo_codes(f1, rel_eb, radius=alphabet // 2)
+        del f1
+        lengths = hd.hd_build_codebook(codes, alphabet, 32)
+        enc = hd.hd_encode(codes, lengths, 128)
+        f = hd.DeviceField.upload(enc, lengths, n, device=dev)
+        fs = hd.DeviceField(f.words, f.nbits, None, 128, f.lengths, alphabet, n)
+        ctx = hd.Context(ctx_dev)
+        row = {"rel_eb": rel_eb, "alphabet": alphabet, "bits_per_code": enc["nbits"] / n}
+        for name, field in (("gap", f), ("selfsync", fs)):
+            ctx.reset_config()
+            row[name + "_launch"] = ctx.autotune([field], [out], stream)
+            ctx.decode(field, out, stream)
+            ok = ctx.status(stream) == 0 and np.array_equal(out.cpu().numpy().view(np.uint16),
+                                                              codes)
+            ms = []
+            for _ in range(steps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.decode(field, out, stream)
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            t = statistics.median(ms)
+            row[name + "_ms"] = t
+            row[name + "_gbps"] = 2.0 * n / (t * 1e-3) / 1e9
+            row[name + "_ok"] = bool(ok and ctx.status(stream) == 0)
+        ctx.close()
+        res.append(row)
+    return {"workload": f"{n} 1D codes per case, S=128 stream; GB/s of uint16 codes out",
+            "cases": res}
+
+
 def mixed_cr_workload(n_seg: int = 32, seg: int = 1 << 21, seed: int = 1005):
     """A 1D field whose compressibility changes along it (segments quantized at
     error bounds 1e-2 .. 1e-6), for the window-class ablation."""
@@ -706,6 +751,7 @@ def run_gpu(args):
     quant.pop("field", None)
     if fields_h is not None:
         extra["decompress_1d"] = run_decompress_1d(hd, torch, dev, stream, flush)
+        extra["skew"] = run_skew(hd, torch, dev, stream, flush)
     if fields_h is not None:
         extra["cr_class_ablation"] = run_cr_ablation(hd, torch, dev, stream, flush, mixed_codes)
         batched, dev_fields = run_batched(hd, torch, dev, stream, flush, fields_h, 3)
