@@ -79,6 +79,7 @@ using hd::FieldDesc;
 constexpr uint32_t kDefaultThreads = 256;
 // first-level table bits when the configuration leaves them open: 13 with
 // 16-bit entries (alphabets up to 4096), else 12
+constexpr double kRunsBelowBits = 4.0;  // mean code length below which counting uses runs
 constexpr uint32_t kDefaultK16 = 13;
 constexpr uint32_t kDefaultK = 12;
 
@@ -276,6 +277,9 @@ int prepare_launch(const hd_ctx* c, std::vector<FieldDesc>& descs, const hd::Lau
   if (s.K == 0) s.K = hd::lut16_usable(kDefaultK16, amax) ? kDefaultK16 : kDefaultK;
   // 16-bit first-level entries when every field's symbols fit 12 bits
   s.lut16 = hd::lut16_usable(s.K, amax) ? 1u : 0u;
+  // run table for counting when codes are short (measured: +24% decode at
+  // 1.9 bits per code, -6% at 9 bits)
+  s.runs = bits_per < kRunsBelowBits ? 1u : 0u;
   if (s.window == 0) {
     // output window: about 1.2x a tile's expected symbol count, rounded up to
     // a multiple of 2048 so that batches of similar code lengths share a shape
@@ -573,7 +577,8 @@ int queue_decode_graph(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::Launc
   c->pinned_busy = true;
 
   const GraphKey key{self_sync, P.s.S,     P.s.threads, P.s.K, P.s.window, P.s.long_cap,
-                     P.s.lut16, cap_f,       cap_t, cap_tab,    reinterpret_cast<uintptr_t>(ws)};
+                     P.s.lut16 | (P.s.runs << 1), cap_f, cap_t, cap_tab,
+                     reinterpret_cast<uintptr_t>(ws)};
   auto it = c->graphs.find(key);
   cudaGraphExec_t exec = nullptr;
   if (it != c->graphs.end()) {

@@ -12,8 +12,9 @@ constexpr uint32_t kTableHeaderBytes = 512;
 // Decode-table header, written by the table kernel.  A decode table is, in
 // order: the header (kTableHeaderBytes), the 32-bit first-level table
 // (uint32[2^K]), the symbols sorted by (code length, symbol) (uint16[A]), the
-// 16-bit first-level table (uint16[2^K], only when A <= 4096 and K <= 15) and
-// the first-level length table (uint8[2^K]); offsets below.
+// 16-bit first-level table (uint16[2^K], only when A <= 4096 and K <= 15),
+// the first-level length table (uint8[2^K]) and the run table (uint8[2^K]);
+// offsets below.
 //
 // Canonical codes occupy, for each length L, the left-aligned 32-bit interval
 //   [first[L] << (32-L), (first[L] + count[L]) << (32-L)),
@@ -60,6 +61,13 @@ __host__ __device__ constexpr uint64_t table_lut16_off(uint32_t K, uint32_t A) {
 }
 __host__ __device__ constexpr uint64_t table_len8_off(uint32_t K, uint32_t A) {
   return table_lut16_off(K, A) + (static_cast<uint64_t>(2) << K);
+}
+// First-level run entry (uint8[2^K] after the length table): the codes that
+// lie wholly within the K bits of the window, decoded one after another from
+// the first: (m << 4) | bits with m in 1..7 codes; 0 when the first code is
+// longer than K bits (or is no code).
+__host__ __device__ constexpr uint64_t table_run8_off(uint32_t K, uint32_t A) {
+  return table_len8_off(K, A) + (static_cast<uint64_t>(1) << K);
 }
 __host__ __device__ constexpr bool lut16_usable(uint32_t K, uint32_t A) {
   return A <= 4096 && K <= 15;

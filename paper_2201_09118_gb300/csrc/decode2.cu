@@ -102,15 +102,17 @@ __host__ __device__ constexpr int write_min_blocks() {
   return 1024 / B;
 }
 
-// E = uint8_t: lengths only (8-bit table).  E = uint16_t / uint32_t: the
-// symbols too (the decode-and-write kernel's table), and each tile's residue
-// sum for decode + reconstruction.
-template <int S, int B, class E>
+// E = uint8_t: lengths only (8-bit table; with RUNS also the run table, for
+// fields of short codes).  E = uint16_t / uint32_t: the symbols too (the
+// decode-and-write kernel's table), and each tile's residue sum for decode +
+// reconstruction.
+template <int S, int B, class E, bool RUNS = false>
 __global__ void __launch_bounds__(B, count_min_blocks<B>())
     k_count(const __grid_constant__ DecodeParams P) {
   using CT = typename CountType<S>::T;
   constexpr bool kSums = sizeof(E) > 1;
-  constexpr Lut kKind = sizeof(E) == 1 ? Lut::k8 : (sizeof(E) == 2 ? Lut::k16 : Lut::k32);
+  constexpr Lut kKind =
+      sizeof(E) == 1 ? (RUNS ? Lut::k8r : Lut::k8) : (sizeof(E) == 2 ? Lut::k16 : Lut::k32);
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* s_lut = smem;  // first-level table
   uint32_t* s_bits = reinterpret_cast<uint32_t*>(smem + lut_bytes(kKind, P.K));
@@ -163,15 +165,28 @@ __global__ void __launch_bounds__(B, count_min_blocks<B>())
         p = end;
       }
       bool bad = false;
+      const uint8_t* run8 = s_lut + (1u << P.K);
       while (p < end) {
         if constexpr (kSums) {
           uint32_t sym;
           p += code_sym_t<E>(T, peek<B>(col, p), sym, bad);
           ssum += sym;
+          ++c;
+        } else if constexpr (RUNS) {
+          // several short codes per lookup when they all start before `end`
+          const uint32_t w = peek<B>(col, p);
+          const uint32_t r = run8[w >> T.shift];
+          if (r && p + (r & 15u) <= end) {
+            p += r & 15u;
+            c += r >> 4;
+          } else {
+            p += code_len8(T, w, bad);
+            ++c;
+          }
         } else {
           p += code_len8(T, peek<B>(col, p), bad);
+          ++c;
         }
-        ++c;
       }
       if (bad) err |= kErrCode;
       else if (p != expect) err |= kErrGap;
@@ -416,8 +431,10 @@ cudaError_t launch_values_s(const DecodeParams& p, const LaunchShape& s, int num
 template <int S, int B>
 cudaError_t launch_sb(const DecodeParams& p, const LaunchShape& s, int num_sms,
                       cudaStream_t stream) {
-  cudaError_t e = launch_persistent(k_count<S, B, uint8_t>, p, B, count_smem_bytes(s), num_sms,
-                                    s.grid, stream);
+  cudaError_t e = s.runs ? launch_persistent(k_count<S, B, uint8_t, true>, p, B,
+                                             count_smem_bytes(s), num_sms, s.grid, stream)
+                         : launch_persistent(k_count<S, B, uint8_t, false>, p, B,
+                                             count_smem_bytes(s), num_sms, s.grid, stream);
   if (e != cudaSuccess) return e;
   e = launch_scan(p, stream);
   if (e != cudaSuccess) return e;
@@ -460,7 +477,7 @@ size_t two_phase_smem_bytes(const LaunchShape& s) {
 
 size_t count_smem_bytes(const LaunchShape& s) {
   const size_t W = s.S / 32 + 1;
-  const size_t b = dev::lut_bytes(dev::Lut::k8, s.K) + W * s.threads * 4;
+  const size_t b = dev::lut_bytes(s.runs ? dev::Lut::k8r : dev::Lut::k8, s.K) + W * s.threads * 4;
   return (b + 15) & ~static_cast<size_t>(15);
 }
 
@@ -496,9 +513,12 @@ template <int S>
 cudaError_t launch_count_s(const DecodeParams& p, const LaunchShape& s, int num_sms,
                            cudaStream_t stream) {
   switch (s.threads) {
-    case 128: return launch_persistent(k_count<S, 128, uint8_t>, p, 128, count_smem_bytes(s), num_sms, s.grid, stream);
-    case 256: return launch_persistent(k_count<S, 256, uint8_t>, p, 256, count_smem_bytes(s), num_sms, s.grid, stream);
-    case 512: return launch_persistent(k_count<S, 512, uint8_t>, p, 512, count_smem_bytes(s), num_sms, s.grid, stream);
+    case 128: return s.runs ? launch_persistent(k_count<S, 128, uint8_t, true>, p, 128, count_smem_bytes(s), num_sms, s.grid, stream)
+                            : launch_persistent(k_count<S, 128, uint8_t, false>, p, 128, count_smem_bytes(s), num_sms, s.grid, stream);
+    case 256: return s.runs ? launch_persistent(k_count<S, 256, uint8_t, true>, p, 256, count_smem_bytes(s), num_sms, s.grid, stream)
+                            : launch_persistent(k_count<S, 256, uint8_t, false>, p, 256, count_smem_bytes(s), num_sms, s.grid, stream);
+    case 512: return s.runs ? launch_persistent(k_count<S, 512, uint8_t, true>, p, 512, count_smem_bytes(s), num_sms, s.grid, stream)
+                            : launch_persistent(k_count<S, 512, uint8_t, false>, p, 512, count_smem_bytes(s), num_sms, s.grid, stream);
     default: return cudaErrorInvalidValue;
   }
 }

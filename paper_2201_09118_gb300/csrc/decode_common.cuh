@@ -426,10 +426,14 @@ __device__ __forceinline__ void window_write_values(uint16_t* s_out, uint32_t* s
 }
 
 // Which first-level table a kernel keeps in shared memory.
-enum class Lut { k32, k16, k8 };
+// k8r: the length table followed by the run table (2 x 2^K bytes).
+enum class Lut { k32, k16, k8, k8r };
 
 __host__ __device__ constexpr uint32_t lut_bytes(Lut kind, uint32_t K) {
-  return kind == Lut::k32 ? (4u << K) : kind == Lut::k16 ? (2u << K) : (1u << K);
+  return kind == Lut::k32 ? (4u << K)
+         : kind == Lut::k16 ? (2u << K)
+         : kind == Lut::k8r ? (2u << K)
+                            : (1u << K);
 }
 
 // Loads the decode table of a field into shared memory (threads [0, nthreads)):

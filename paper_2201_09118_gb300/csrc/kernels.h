@@ -26,6 +26,7 @@ struct LaunchShape {
   uint32_t long_cap; // symbols of long codes kept in shared memory
   uint32_t grid;     // persistent blocks (0: full occupancy)
   uint32_t lut16;    // 1: the decode-and-write kernel uses 16-bit first-level entries
+  uint32_t runs;     // 1: the count kernel takes several short codes per lookup (run table)
 };
 
 // Dynamic shared memory of the single-pass gap-array kernel.

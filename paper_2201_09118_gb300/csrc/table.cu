@@ -39,6 +39,7 @@ __device__ void build_table(const FieldDesc& F, uint32_t K) {
   uint16_t* sorted = reinterpret_cast<uint16_t*>(tb + table_sorted_off(K));
   uint16_t* lut16 = reinterpret_cast<uint16_t*>(tb + table_lut16_off(K, A));
   uint8_t* len8 = reinterpret_cast<uint8_t*>(tb + table_len8_off(K, A));
+  uint8_t* run8 = reinterpret_cast<uint8_t*>(tb + table_run8_off(K, A));
   const bool with16 = lut16_usable(K, A);
 
   if (t < 34) {
@@ -130,12 +131,25 @@ __device__ void build_table(const FieldDesc& F, uint32_t K) {
     const uint32_t w = p << (32 - K);
     uint32_t L = 1;
     while (L <= 32 && static_cast<uint64_t>(w) >= s_end[L]) ++L;
-    uint32_t e, e16, e8;
+    uint32_t e, e16, e8, r8 = 0;
     if (L <= K && L <= maxlen) {
       const uint32_t rank = (w >> (32 - L)) + s_base[L];
       e = (L << 16) | sorted[rank];
       e16 = (L << 12) | (sorted[rank] & 0xFFFu);
       e8 = L;
+      // further codes wholly within the K known bits: a code of length
+      // L2 <= the bits left is fixed by them (the limits are left-aligned)
+      uint32_t used = L, m = 1;
+      while (m < 7 && used < K) {
+        const uint32_t rem = K - used;
+        const uint32_t w2 = w << used;
+        uint32_t L2 = 1;
+        while (L2 <= rem && static_cast<uint64_t>(w2) >= s_end[L2]) ++L2;
+        if (L2 > rem || L2 > maxlen) break;
+        used += L2;
+        ++m;
+      }
+      r8 = (m << 4) | used;
     } else {
       // length of the code at the last window with this prefix
       const uint32_t w_last = w | ((1u << (32 - K)) - 1u);
@@ -150,6 +164,7 @@ __device__ void build_table(const FieldDesc& F, uint32_t K) {
     lut[p] = e;
     if (with16) lut16[p] = static_cast<uint16_t>(e16);
     len8[p] = static_cast<uint8_t>(e8);
+    run8[p] = static_cast<uint8_t>(r8);
   }
 }
 
@@ -183,7 +198,7 @@ cudaError_t launch_prepare(const PrepParams& p, cudaStream_t stream) {
 }
 
 size_t table_bytes(uint32_t K, uint32_t alphabet) {
-  const size_t b = table_len8_off(K, alphabet) + (static_cast<size_t>(1) << K);
+  const size_t b = table_run8_off(K, alphabet) + (static_cast<size_t>(1) << K);
   return (b + 255) & ~static_cast<size_t>(255);
 }
 
