@@ -89,3 +89,12 @@ def test_lorenzo_radius_boundary_and_outlier_list():
     assert np.array_equal(g["out_idx"], np.flatnonzero(~inl).astype(np.uint64))
     assert np.array_equal(g["out_val"], d[~inl].astype(np.int32))
     assert g["codes"][1] == 2 * R - 1 and g["codes"][2] == 1
+
+
+def test_field3d_quantized_outliers_match_zero_codes():
+    g = synth.field3d_quantized(24, rel_eb=1e-4, noise=0.01, seed=5, keep_field=True)
+    assert g["codes"].size == 24 ** 3 and g["field"].shape == (24, 24, 24)
+    zero = np.flatnonzero(g["codes"] == 0).astype(np.uint64)
+    assert np.array_equal(zero, g["out_idx"])
+    assert g["out_val"].dtype == np.int32 and g["out_val"].size == zero.size
+    assert np.all(np.abs(g["out_val"].astype(np.int64)) >= 512)
