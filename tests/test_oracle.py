@@ -246,6 +246,45 @@ def test_kraft_equality_random_histograms():
         assert all((lens > 0) == (freq > 0))
 
 
+# ----------------------------------------------------------------------------
+# histogram (the symbol frequencies Huffman's construction starts from, Sec. II-B)
+# ----------------------------------------------------------------------------
+
+
+def test_histogram_fig1_string_counted_by_hand(golden):
+    # BACACCBDBAAEBBA: A at 2, 4, 10, 11, 15; B at 1, 7, 9, 13, 14; C at 3, 5, 6;
+    # D at 8; E at 12 (1-based positions, counted by hand)
+    string = golden("fig1_gap_array.txt")["string"][0]
+    assert string == "BACACCBDBAAEBBA"
+    x = np.array(["ABCDE".index(ch) for ch in string], np.uint16)
+    assert oracle.histogram(x, 5).tolist() == [5, 5, 3, 1, 1]
+    # unused symbols of a larger alphabet count zero
+    assert oracle.histogram(x, 9).tolist() == [5, 5, 3, 1, 1, 0, 0, 0, 0]
+
+
+def test_histogram_against_independent_count():
+    from collections import Counter
+    x = synth.laplace_codes(200003, scale=40.0, seed=21)
+    x[::997] = 1023  # the alphabet's last symbol
+    x[5] = 0
+    ref = Counter(int(v) for v in x.tolist())
+    got = oracle.histogram(x, 1024)
+    assert got.dtype == np.uint64 and got.size == 1024
+    for sym in range(1024):
+        assert int(got[sym]) == ref.get(sym, 0), sym
+    assert int(got.sum()) == x.size
+
+
+def test_histogram_edges_and_errors():
+    assert oracle.histogram(np.zeros(0, np.uint16), 4).tolist() == [0, 0, 0, 0]
+    x = np.array([65535, 0, 65535], np.uint16)
+    h = oracle.histogram(x, 65536)
+    assert int(h[65535]) == 2 and int(h[0]) == 1 and int(h.sum()) == 3
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.histogram(np.array([0, 4, 1], np.uint16), 4)  # 4 is outside [0, 4)
+    assert e.value.code == oracle.ERR_SYMBOL
+
+
 def test_single_and_no_symbol():
     freq = np.zeros(8, np.uint64)
     assert oracle.code_lengths(freq).tolist() == [0] * 8
