@@ -124,7 +124,9 @@ typedef struct hd_config {
                            self-synchronisation: 64, 128 or 256 (512 acts as
                            256; 0 = 256); hd_sync_points always uses the
                            field's S */
-  uint32_t threads;     /* threads per block = subsequences per tile: 128, 256, 512 */
+  uint32_t threads;     /* threads per block: 128, 256, 512 (two phases: one
+                           subsequence per thread, a tile per block); one pass
+                           also 1024 (a tile per warp) */
   uint32_t window;      /* shared-memory output window in symbols (Alg. 1 buffer);
                            0 = sized from the field's mean code length */
   uint32_t lut_bits;    /* first-level decode-table index bits, 8 .. 15 (0 = 13
@@ -139,6 +141,14 @@ typedef struct hd_config {
                            one decode-and-write launch per class runs with a
                            window sized for that class's largest tile (capped
                            by shared memory) */
+  uint32_t decoder;     /* gap-array decodes: 0 = automatic (one pass for a single
+                           field, two phases for batches, CR classes and
+                           decode + reconstruction), 1 = two phases (count
+                           kernel, tile scan, decode-and-write kernel), 2 = one
+                           pass: each warp decodes 32 subsequences once into
+                           shared memory, takes its output index from a
+                           look-back over the tiles before it and writes
+                           through its window (single fields only) */
 } hd_config;
 
 /* Sets the launch shape used by later decodes on this context (NULL resets to
@@ -235,7 +245,10 @@ int hd_decode_host(hd_ctx* ctx, const hd_field* f, uint16_t* host_out, void* str
  * work.  The first
  * call on each device does a one-time set-up (it looks up the array's device
  * address with that device current); make that first call before any stream
- * capture.  All calls on a device share the one array, which keeps the last
+ * capture.  That address is kept for the life of the process: after a
+ * cudaDeviceReset (or anything else that recreates the device's primary
+ * context) it would be stale, so such a reset is not supported in a process
+ * that has called this entry point.  All calls on a device share the one array, which keeps the last
  * call's contents: each call clears the parts that must start at zero, but
  * calls whose GPU work overlaps (e.g. issued on two streams at once) race on
  * it and give wrong results.  The call waits for its work on `stream` and
@@ -268,6 +281,11 @@ typedef struct hd_serve_config {
   uint32_t direct;       /* 1: one hd_decode launch per request instead of a
                             batch (requires max_batch == 1; the baseline the
                             batched server is compared with) */
+  uint32_t watchdog_us;  /* limit on a batch's time on the GPU, microseconds
+                            (0 = 10 s).  Past it, the batch's requests complete
+                            with status HD_ERR_TIMEOUT and no output; the slot
+                            and their output memory stay held (the GPU may
+                            still write there) until the work really ends */
 } hd_serve_config;
 
 typedef struct hd_result {
@@ -281,6 +299,8 @@ typedef struct hd_result {
 typedef struct hd_serve_stats_t {
   uint64_t submitted, completed, batches, pending, in_flight;
   uint64_t budget_bytes, used_bytes, peak_bytes;
+  uint64_t timed_out_batches; /* batches past the watchdog, still on the GPU */
+  uint64_t retired_batches;   /* timed-out batches that ended later */
 } hd_serve_stats_t;
 
 /* Creates a server on `device` (`shape` may be NULL: default or autotuned
@@ -398,6 +418,21 @@ int hd_encode_device(hd_ctx* ctx, const uint16_t* d_codes, uint64_t n, const uin
  * the summed device time in milliseconds and the launch count, then clears. */
 int hd_profile(hd_ctx* ctx, int enable);
 int hd_kernel_time(hd_ctx* ctx, double* ms, uint64_t* launches);
+
+/* Per-phase device time of the single-field decodes queued on this context
+ * while profiling (hd_profile) since the last call, in milliseconds summed over
+ * those decodes, mirroring the phases the paper times (Sec. V-B):
+ *   ms[0] synchronisation: finding the subsequence starts without a gap array
+ *         (Sec. III-B2 steps 1-2, the self-synchronising kernels);
+ *   ms[1] counting the codewords of every subsequence (gap-array count kernel);
+ *   ms[2] output indices: the prefix sum over tiles (Sec. III-B2 step 3);
+ *   ms[3] decode and write (Algorithm 1); for the one-pass decoder, whose one
+ *         kernel counts, takes its indices and writes, the whole pass.
+ * With profiling on, the two-phase kernels are queued one phase at a time with
+ * an event between phases.  *decodes receives the number of decodes summed.
+ * Waits for the events and clears them.  Batches (graph launches) are not
+ * split into phases. */
+int hd_phase_times(hd_ctx* ctx, double* ms, uint64_t* decodes);
 
 /* Number of kernel launches the context has issued since creation. */
 uint64_t hd_launch_count(hd_ctx* ctx);

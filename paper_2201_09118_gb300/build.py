@@ -54,8 +54,8 @@ def _stale(lib: str) -> bool:
 def build(force: bool = False, verbose: bool = False, extra_flags=(), out_dir: str = None) -> str:
     """Compile and link libhd.so if any source changed; returns its path.
 
-    ``extra_flags``/``out_dir`` build a variant elsewhere (e.g. the debug build
-    with -DHD_PHASE_TIMERS); the default build goes to _build/libhd.so."""
+    ``extra_flags``/``out_dir`` build a variant elsewhere (extra nvcc flags,
+    another directory); the default build goes to _build/libhd.so."""
     build_dir = out_dir or BUILD
     lib = os.path.join(build_dir, "libhd.so")
     with _lock:

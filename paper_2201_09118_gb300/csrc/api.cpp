@@ -44,6 +44,9 @@ struct hd_ctx {
   bool profile = false;
   std::vector<cudaEvent_t> events;
   size_t events_used = 0;
+  // per-phase timing while profiling: (phase, event before, event after)
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> phase_recs;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans;  // hd_kernel_time spans
   uint64_t launches = 0;
   hd::LaunchShape last_shape{};  // launch shape of the last decode
   // graph launches (hd_decode_batch)
@@ -171,6 +174,14 @@ uint32_t default_decoder_S(uint32_t stream_S, bool gap) {
   return stream_S < 256 ? 256 : stream_S;
 }
 
+// A shape for the two-phase kernels (threads of one block = one tile of
+// subsequences: 128, 256 or 512).
+hd::LaunchShape two_phase_shape(hd::LaunchShape s) {
+  if (s.threads != 128 && s.threads != 256 && s.threads != 512) s.threads = kDefaultThreads;
+  s.decoder = 1;
+  return s;
+}
+
 hd::LaunchShape shape_for(const hd_ctx* c, uint32_t stream_S, bool gap) {
   hd::LaunchShape s{};
   s.S = c->cfg.subseq_bits ? c->cfg.subseq_bits : default_decoder_S(stream_S, gap);
@@ -178,7 +189,7 @@ hd::LaunchShape shape_for(const hd_ctx* c, uint32_t stream_S, bool gap) {
   s.K = c->cfg.lut_bits;  // 0: chosen per launch
   s.window = c->cfg.window;  // 0: chosen per launch
   s.grid = 0;
-  return s;
+  return two_phase_shape(s);
 }
 
 uint64_t tiles_for(uint64_t nsub, const hd::LaunchShape& s) {
@@ -192,6 +203,18 @@ cudaEvent_t next_event(hd_ctx* c) {
     c->events.push_back(e);
   }
   return c->events[c->events_used++];
+}
+
+// Phases of hd_phase_times.
+enum PhaseId { kPhSync = 0, kPhCount = 1, kPhIndex = 2, kPhWrite = 3 };
+
+// Records an event on `st` that closes the phase opened by *open (when
+// profiling) and opens the next one; returns the new event.
+cudaEvent_t phase_mark(hd_ctx* c, cudaStream_t st, int phase, cudaEvent_t open) {
+  cudaEvent_t e = next_event(c);
+  cudaEventRecord(e, st);
+  if (open) c->phase_recs.emplace_back(phase, open, e);
+  return e;
 }
 
 // Fills the per-field part of a descriptor (device pointers, sizes).
@@ -451,10 +474,113 @@ struct ValueArgs {
 // Queues a decode of fields that all use the same strategy with direct
 // kernel launches (sizes as kernel parameters).  With `va` (one gap-array
 // field): values instead of codes.
-int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape& shape,
+// Time limit of one look-back wait of the one-pass decoder (SM clock cycles,
+// about 2 s at GB300 clocks); a wait that runs out reports HD_ERR_TIMEOUT.
+constexpr uint64_t kLookbackTimeoutCycles = 4000000000ull;
+
+// Column symbols per lane of the one-pass decoder for a field of `bits_per`
+// bits per code: about 1.3x a subsequence's expected codeword count, even.
+uint32_t one_pass_cmax(uint32_t S, double bits_per) {
+  const double want = 1.3 * S / std::max(bits_per, 0.25) + 2.0;
+  uint32_t c = static_cast<uint32_t>(std::ceil(want));
+  c = (c + 1) & ~1u;
+  return std::min<uint32_t>(std::max<uint32_t>(c, 4), std::min<uint32_t>(S, 512));
+}
+
+// Queues a one-pass decode of one gap-array field (decode_warp.cu).
+// Workspace: error word | ticket, abort flag | one look-back state per tile
+// (the three cleared by the table kernel) | decode table.
+int queue_decode_one_pass(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape& shape,
+                          cudaStream_t st) {
+  FieldDesc& d = descs[0];
+  hd::LaunchShape s = shape;
+  const double bits_per =
+      static_cast<double>(d.nbits) / static_cast<double>(d.n ? d.n : 1);
+  s.long_cap = static_cast<uint32_t>(align_up(std::min<uint32_t>(d.alphabet, 4096), 8));
+  if (s.K == 0) s.K = hd::lut16_usable(kDefaultK16, d.alphabet) ? kDefaultK16 : kDefaultK;
+  s.lut16 = hd::lut16_usable(s.K, d.alphabet) ? 1u : 0u;
+  s.runs = 0;
+  s.decoder = 2;
+  s.cmax = one_pass_cmax(s.S, bits_per);
+  s.window = 32 * s.cmax;
+  const size_t budget = static_cast<size_t>(c->max_smem) - 2048;
+  const bool fixed_threads = s.threads != 0;
+  if (!fixed_threads) {
+    s.threads = 1024;
+    while (s.threads > 128 && hd::warp_decode_smem_bytes(s) > budget) s.threads >>= 1;
+  }
+  if (s.threads != 128 && s.threads != 256 && s.threads != 512 && s.threads != 1024)
+    return HD_ERR_ARG;
+  // the column is an optimisation (overflowing lanes decode again), so it
+  // shrinks to fit shared memory
+  while (s.cmax > 4 && hd::warp_decode_smem_bytes(s) > budget) s.cmax -= 2;
+  s.window = 32 * s.cmax;
+  if (hd::warp_decode_smem_bytes(s) > budget) return HD_ERR_ARG;
+  d.unit_begin = 0;
+  d.nunits = (d.nsub + 31) / 32;
+  d.count_begin = 0;
+  const size_t tk_off = 16, st_off = 32;
+  const size_t zero = align_up(st_off + 8 * d.nunits, 16);
+  const size_t tab_off = align_up(zero, 256);
+  const size_t need = tab_off + hd::table_bytes(s.K, d.alphabet);
+  int rc = ensure_ws(c, need);
+  if (rc) return rc;
+  char* ws = c->ws;
+  d.table = reinterpret_cast<const hd::TableHeader*>(ws + tab_off);
+  d.err = reinterpret_cast<uint32_t*>(ws);
+  hd::PrepParams pp{};
+  pp.f0 = d;
+  pp.nfields = 1;
+  pp.table_blocks = 1;
+  pp.K = s.K;
+  pp.zero_ptr = reinterpret_cast<uint4*>(ws);
+  pp.zero_vec = zero / 16;
+  pp.zero_blocks = static_cast<uint32_t>(std::min<uint64_t>((pp.zero_vec + 4095) / 4096, 64));
+  if (pp.zero_blocks == 0) pp.zero_blocks = 1;
+  hd::DecodeParams dp{};
+  dp.f0 = d;
+  dp.nfields = 1;
+  dp.K = s.K;
+  dp.window = s.window;
+  dp.cmax = s.cmax;
+  dp.long_cap = s.long_cap;
+  dp.total_units = d.nunits;
+  dp.unit_state = reinterpret_cast<uint64_t*>(ws + st_off);
+  dp.ticket = reinterpret_cast<uint32_t*>(ws + tk_off);
+  dp.abort_flag = reinterpret_cast<uint32_t*>(ws + tk_off) + 1;
+  dp.timeout_cycles = kLookbackTimeoutCycles;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->profile) {
+    e0 = next_event(c);
+    e1 = next_event(c);
+  }
+  cudaError_t e = hd::launch_prepare(pp, st);
+  if (e == cudaSuccess && c->profile) cudaEventRecord(e0, st);
+  if (e == cudaSuccess) e = hd::launch_decode_warp(dp, s, c->num_sms, st);
+  if (c->profile) {
+    cudaEventRecord(e1, st);
+    c->spans.emplace_back(e0, e1);
+    c->phase_recs.emplace_back(kPhWrite, e0, e1);  // one kernel does every phase
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return HD_ERR_CUDA;
+  }
+  c->launches += 2;
+  c->err_off = 0;
+  c->err_count = 1;
+  c->recon_active = false;
+  c->last_shape = s;
+  return HD_OK;
+}
+
+int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape& shape_in,
                  bool self_sync, bool sync_only, cudaStream_t st,
                  const ValueArgs* va = nullptr) {
   const uint32_t nf = static_cast<uint32_t>(descs.size());
+  if (!self_sync && !sync_only && !va && nf == 1 && shape_in.decoder == 2 && !c->cfg.cr_classes)
+    return queue_decode_one_pass(c, descs, shape_in, st);
+  const hd::LaunchShape shape = two_phase_shape(shape_in);
   Prepared P;
   int rc = prepare_launch(c, descs, shape, self_sync, P);
   if (rc) return rc;
@@ -500,7 +626,23 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
   // the timed span starts after the table kernel
   cudaError_t e = hd::launch_prepare(pp, st);
   if (e == cudaSuccess && c->profile) cudaEventRecord(e0, st);
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && c->profile && !va && !nclass) {
+    // the same kernels one phase at a time, with an event between phases
+    cudaEvent_t m = e0;
+    if (self_sync) {
+      e = hd::launch_sync(dp, P.s, c->num_sms, st);
+      m = phase_mark(c, st, kPhSync, m);
+    } else {
+      e = hd::launch_phase(dp, P.s, hd::Phase::kCount, c->num_sms, st);
+      m = phase_mark(c, st, kPhCount, m);
+    }
+    if (e == cudaSuccess && !sync_only) {
+      e = hd::launch_phase(dp, P.s, hd::Phase::kScan, c->num_sms, st);
+      m = phase_mark(c, st, kPhIndex, m);
+      if (e == cudaSuccess) e = hd::launch_phase(dp, P.s, hd::Phase::kWrite, c->num_sms, st);
+      m = phase_mark(c, st, kPhWrite, m);
+    }
+  } else if (e == cudaSuccess) {
     if (self_sync) {
       e = hd::launch_sync(dp, P.s, c->num_sms, st);
       if (e == cudaSuccess && !sync_only) e = hd::launch_write(dp, P.s, c->num_sms, st);
@@ -515,7 +657,10 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
       e = hd::launch_decode_two_phase(dp, P.s, c->num_sms, st);
     }
   }
-  if (c->profile) cudaEventRecord(e1, st);
+  if (c->profile) {
+    cudaEventRecord(e1, st);
+    c->spans.emplace_back(e0, e1);
+  }
   if (e != cudaSuccess) return HD_ERR_CUDA;
   c->launches += kernels_per_launch(self_sync, sync_only) + (va ? 2 : 0);
   c->err_off = L.err;
@@ -530,9 +675,10 @@ int queue_decode(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape
 // batch that fits: field and tile counts travel in the device-side launch
 // header and the descriptors, both copied in before the replay from pinned
 // host memory.  Capacities are powers of two, so a context holds few graphs.
-int queue_decode_graph(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape& shape,
+int queue_decode_graph(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape& shape_in,
                        bool self_sync, cudaStream_t st) {
   const uint32_t nf = static_cast<uint32_t>(descs.size());
+  const hd::LaunchShape shape = two_phase_shape(shape_in);
   Prepared P;
   int rc = prepare_launch(c, descs, shape, self_sync, P);
   if (rc) return rc;
@@ -616,7 +762,10 @@ int queue_decode_graph(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::Launc
     cudaEventRecord(e0, st);
   }
   const cudaError_t e = cudaGraphLaunch(exec, st);
-  if (c->profile) cudaEventRecord(e1, st);
+  if (c->profile) {
+    cudaEventRecord(e1, st);
+    c->spans.emplace_back(e0, e1);
+  }
   if (e != cudaSuccess) return HD_ERR_CUDA;
   c->launches += kernels_per_launch(self_sync, false);
   c->err_off = L.err;
@@ -663,7 +812,8 @@ hd::LaunchShape group_shape(const hd_ctx* c, const hd_field* fs, const std::vect
     syms += fs[i].n;
   }
   const hd_config& k = c->cfg;
-  const bool user = k.subseq_bits || k.threads || k.window || k.lut_bits || k.cr_classes;
+  const bool user =
+      k.subseq_bits || k.threads || k.window || k.lut_bits || k.cr_classes || k.decoder;
   hd_config use = k;
   if (!user) {
     auto it = c->tuned.find(tune_key(gap, maxS, bits, syms));
@@ -672,9 +822,13 @@ hd::LaunchShape group_shape(const hd_ctx* c, const hd_field* fs, const std::vect
   hd::LaunchShape s{};
   s.S = use.subseq_bits ? use.subseq_bits : default_decoder_S(maxS ? maxS : 128, gap);
   if (!gap && s.S > 256) s.S = 256;
-  s.threads = use.threads ? use.threads : kDefaultThreads;
+  s.threads = use.threads;  // 0: chosen per launch
   s.K = use.lut_bits;  // 0: chosen per launch
   s.window = use.window;
+  // one pass decodes single gap-array fields; groups of several fields and
+  // self-synchronisation run the two-phase kernels
+  s.decoder = gap && idx.size() == 1 && use.decoder != 1 && !use.cr_classes ? 2u : 1u;
+  if (s.decoder == 1) s = two_phase_shape(s);
   return s;
 }
 
@@ -787,7 +941,7 @@ int decode_host_pipelined(hd_ctx* c, const hd_field* f, uint16_t* host_out, cuda
   const size_t len_b = align_up(f->alphabet, 256);
   const size_t out_b = align_up(f->n * 2, 256);
   hd_field d = *f;  // device copy of the field, pointers into the staging area
-  hd::LaunchShape shape = field_shape(c, &d, true);
+  hd::LaunchShape shape = two_phase_shape(field_shape(c, &d, true));
   if (shape.S % f->subseq_bits) return HD_OK;  // not pipelined
   std::vector<FieldDesc> descs(1);
   {
@@ -883,7 +1037,10 @@ int decode_host_pipelined(hd_ctx* c, const hd_field* f, uint16_t* host_out, cuda
       return HD_ERR_CUDA;
     c->launches += 3;
   }
-  if (c->profile) cudaEventRecord(e1, st);
+  if (c->profile) {
+    cudaEventRecord(e1, st);
+    c->spans.emplace_back(e0, e1);
+  }
   // symbols back to the host, chunk by chunk, as their ends become known
   uint64_t done = 0;
   for (uint32_t j = 0; j < nch; ++j) {
@@ -975,7 +1132,9 @@ int hd_set_config(hd_ctx* c, const hd_config* cfg) {
     return HD_OK;
   }
   if (cfg->subseq_bits && !valid_S(cfg->subseq_bits) && cfg->subseq_bits != 512) return HD_ERR_ARG;
-  if (cfg->threads && cfg->threads != 128 && cfg->threads != 256 && cfg->threads != 512)
+  if (cfg->decoder > 2) return HD_ERR_ARG;
+  if (cfg->threads && cfg->threads != 128 && cfg->threads != 256 && cfg->threads != 512 &&
+      !(cfg->threads == 1024 && cfg->decoder == 2))
     return HD_ERR_ARG;
   if (cfg->lut_bits && (cfg->lut_bits < 8 || cfg->lut_bits > 15)) return HD_ERR_ARG;
   if (cfg->cr_classes && (cfg->cr_classes < 2 || cfg->cr_classes > 32)) return HD_ERR_ARG;
@@ -993,6 +1152,7 @@ int hd_get_config(hd_ctx* c, hd_config* cfg) {
   cfg->window = c->cfg.window ? c->cfg.window : c->last_shape.window;
   cfg->lut_bits = c->cfg.lut_bits ? c->cfg.lut_bits : c->last_shape.K;
   cfg->cr_classes = c->cfg.cr_classes;
+  cfg->decoder = c->cfg.decoder ? c->cfg.decoder : c->last_shape.decoder;
   return HD_OK;
 }
 
@@ -1113,11 +1273,47 @@ int hd_autotune(hd_ctx* c, const hd_field* fs, uint32_t nf, uint16_t* const* d_o
     const uint32_t K_list[4] = {11, 12, 13, 14};
     double best_ms = 1e30;
     hd_config best_cfg{};
+    // a single gap-array field: the one-pass decoder's shapes too (direct
+    // launches, as hd_decode runs them)
+    if (!ss && idx.size() == 1) {
+      const uint32_t i = idx[0];
+      for (uint32_t S : S_list) {
+        if (S < 128 || S % maxS) continue;
+        for (uint32_t B : {512u, 1024u}) {
+          for (uint32_t K : {12u, 13u, 14u}) {
+            c->cfg = hd_config{S, B, 0, K, 0, 2};
+            const hd::LaunchShape sh = group_shape(c, fs, idx, true);
+            double ms = 1e30;
+            bool ok = true;
+            for (int rep = 0; rep < 4 && ok; ++rep) {
+              std::vector<FieldDesc> dd(1);
+              fill_desc(dd[0], &fs[i], sh, d_outs[i]);
+              cudaEventRecord(t0, st);
+              const int r = queue_decode(c, dd, sh, false, false, st);
+              cudaEventRecord(t1, st);
+              std::vector<uint32_t> bits_v;
+              if (r || read_errors(c, stream, bits_v) != HD_OK) {
+                ok = false;
+                break;
+              }
+              for (uint32_t b : bits_v) ok &= b == 0;
+              float t = 0;
+              cudaEventElapsedTime(&t, t0, t1);
+              if (rep) ms = std::min(ms, static_cast<double>(t));
+            }
+            if (ok && ms < best_ms) {
+              best_ms = ms;
+              best_cfg = hd_config{S, B, 0, K, 0, 2};
+            }
+          }
+        }
+      }
+    }
     for (uint32_t S : S_list) {
       if (ss ? (S > 256) : (S < 128 || S % maxS)) continue;
       for (uint32_t B : B_list) {
         for (uint32_t K : K_list) {
-          c->cfg = hd_config{S, B, 0, K};
+          c->cfg = hd_config{S, B, 0, K, 0, 1};
           std::vector<FieldDesc> d;
           const hd::LaunchShape sh = group_shape(c, fs, idx, !ss);
           for (uint32_t i : idx) {
@@ -1148,7 +1344,7 @@ int hd_autotune(hd_ctx* c, const hd_field* fs, uint32_t nf, uint16_t* const* d_o
           }
           if (ok && ms < best_ms) {
             best_ms = ms;
-            best_cfg = hd_config{S, B, 0, K};
+            best_cfg = hd_config{S, B, 0, K, 0, 1};
           }
         }
       }
@@ -1542,7 +1738,10 @@ static int reconstruct_locked(hd_ctx* c, const uint16_t* d_codes, const hd_loren
       launches += 3;
     }
   }
-  if (e == cudaSuccess && c->profile) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess && c->profile) {
+    e = cudaEventRecord(e1, st);
+    c->spans.emplace_back(e0, e1);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     c->host_status = HD_ERR_CUDA;
@@ -1610,22 +1809,45 @@ int hd_kernel_time(hd_ctx* c, double* ms, uint64_t* launches) {
   DeviceGuard g(c->device);
   double total = 0;
   uint64_t n = 0;
-  for (size_t k = 0; k + 1 < c->events_used; k += 2) {
-    if (cudaEventSynchronize(c->events[k + 1]) != cudaSuccess) {
+  for (const auto& pr : c->spans) {
+    if (cudaEventSynchronize(pr.second) != cudaSuccess) {
       cudaGetLastError();
       return HD_ERR_CUDA;
     }
     float t = 0;
-    if (cudaEventElapsedTime(&t, c->events[k], c->events[k + 1]) != cudaSuccess) {
+    if (cudaEventElapsedTime(&t, pr.first, pr.second) != cudaSuccess) {
       cudaGetLastError();
       return HD_ERR_CUDA;
     }
     total += t;
     ++n;
   }
-  c->events_used = 0;
+  c->spans.clear();
+  if (c->phase_recs.empty()) c->events_used = 0;
   *ms = total;
   *launches = n;
+  return HD_OK;
+}
+
+int hd_phase_times(hd_ctx* c, double* ms, uint64_t* decodes) {
+  if (!c || !ms || !decodes) return HD_ERR_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  for (int k = 0; k < 4; ++k) ms[k] = 0;
+  uint64_t n = 0;
+  for (const auto& r : c->phase_recs) {
+    const cudaEvent_t a = std::get<1>(r), b = std::get<2>(r);
+    float t = 0;
+    if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&t, a, b) != cudaSuccess) {
+      cudaGetLastError();
+      return HD_ERR_CUDA;
+    }
+    ms[std::get<0>(r)] += t;
+    n += std::get<0>(r) == kPhWrite ? 1 : 0;
+  }
+  c->phase_recs.clear();
+  if (c->spans.empty()) c->events_used = 0;
+  *decodes = n;
   return HD_OK;
 }
 

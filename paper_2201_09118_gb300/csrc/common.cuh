@@ -29,6 +29,7 @@ struct TableHeader {
   uint64_t end[34];  // end[L]: exclusive left-aligned limit of codes of length <= L
   uint32_t base[34]; // start[L] - first[L] (mod 2^32): rank = (w >> (32-L)) + base[L]
   uint32_t long0;    // rank of the first code longer than K (codes sorted by length)
+  uint32_t minlen;   // shortest code length in use (0 if no symbol is used)
 };
 static_assert(sizeof(TableHeader) <= kTableHeaderBytes, "table header too large");
 

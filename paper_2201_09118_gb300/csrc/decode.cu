@@ -30,9 +30,6 @@ namespace {
 
 using namespace dev;
 
-constexpr int kLbPerLane = 8;                 // states each look-back lane reads
-constexpr int kLbSpan = 32 * kLbPerLane;      // tiles per look-back round trip
-
 // One pass from `p` to `end`: symbols into the scratch column while they fit
 // (cmax slots), codewords counted to the end.  Returns the stop position.
 template <int B>
@@ -53,65 +50,6 @@ __device__ __forceinline__ uint32_t decode_pass(const Tables& T, const uint32_t*
   c = j;
   return p;
 }
-
-__device__ __forceinline__ void lb_load(const uint64_t* st, int64_t j, int64_t lo, int lane,
-                                        uint64_t (&s)[kLbPerLane]) {
-#pragma unroll
-  for (int k = 0; k < kLbPerLane; ++k) {
-    const int64_t idx = j - kLbPerLane * lane - k;
-    s[k] = idx >= lo ? ld_relaxed(st + idx) : kStateInc;
-  }
-}
-
-// Look-back over tiles for the count prefix (warp 0).  Publishes the tile's
-// aggregate, sums predecessors back to the nearest inclusive prefix, then
-// publishes its own inclusive prefix.  Returns the exclusive prefix.
-__device__ __forceinline__ uint64_t lookback_counts(const DecodeParams& P, uint64_t g,
-                                                    uint64_t first, uint64_t C, uint32_t* err) {
-  const int lane = threadIdx.x & 31;
-  uint64_t* st = P.unit_state;
-  if (g == first) {
-    if (lane == 0) st_relaxed(st + g, kStateInc | C);
-    return 0;
-  }
-  if (lane == 0) st_relaxed(st + g, kStateAgg | C);
-  uint64_t excl = 0;
-  int64_t j = static_cast<int64_t>(g) - 1;
-  const int64_t lo = static_cast<int64_t>(first);
-  const uint64_t t0 = static_cast<uint64_t>(clock64());
-  for (;;) {
-    uint64_t s[kLbPerLane];
-    lb_load(st, j, lo, lane, s);
-    bool has_inc = false, notready = false;
-    uint64_t sum = 0;
-#pragma unroll
-    for (int k = 0; k < kLbPerLane; ++k) {
-      if (!has_inc) {
-        const uint32_t flag = static_cast<uint32_t>(s[k] >> 62);
-        notready |= flag == 0u;
-        sum += s[k] & kStateValMask;
-        has_inc = flag == 2u;
-      }
-    }
-    const uint32_t inc = __ballot_sync(0xffffffffu, has_inc);
-    const uint32_t need = inc ? (((inc & (0u - inc)) << 1) - 1u) : 0xffffffffu;
-    if (__ballot_sync(0xffffffffu, notready) & need) {
-      bool go = true;
-      if (lane == 0) go = backoff_wait(P, t0);
-      if (!__shfl_sync(0xffffffffu, go, 0)) {
-        if (lane == 0) atomicOr(err, kErrTimeout);
-        break;
-      }
-      continue;
-    }
-    excl += warp_sum_u64((need >> lane) & 1u ? sum : 0ull);
-    if (inc) break;
-    j -= kLbSpan;
-  }
-  if (lane == 0) st_relaxed(st + g, kStateInc | ((excl + C) & kStateValMask));
-  return excl;
-}
-
 
 template <int S, int B>
 __global__ void __launch_bounds__(B) k_decode(const __grid_constant__ DecodeParams P) {

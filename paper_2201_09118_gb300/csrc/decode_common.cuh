@@ -198,6 +198,71 @@ __device__ __forceinline__ bool backoff_wait(const DecodeParams& P, uint64_t t0)
   return true;
 }
 
+// Decoupled look-back over per-tile states (the output-index prefix of
+// Sec. III-B2 step 3 across tiles): each lane reads kLbPerLane states, so one
+// round trip through L2 covers kLbSpan predecessor tiles.
+constexpr int kLbPerLane = 8;
+constexpr int kLbSpan = 32 * kLbPerLane;
+
+__device__ __forceinline__ void lb_load(const uint64_t* st, int64_t j, int64_t lo, int lane,
+                                        uint64_t (&s)[kLbPerLane]) {
+#pragma unroll
+  for (int k = 0; k < kLbPerLane; ++k) {
+    const int64_t idx = j - kLbPerLane * lane - k;
+    s[k] = idx >= lo ? ld_relaxed(st + idx) : kStateInc;
+  }
+}
+
+// Look-back over tiles for the count prefix (one whole warp).  Publishes the tile's
+// aggregate, sums predecessors back to the nearest inclusive prefix, then
+// publishes its own inclusive prefix.  Returns the exclusive prefix.
+__device__ __forceinline__ uint64_t lookback_counts(const DecodeParams& P, uint64_t g,
+                                                    uint64_t first, uint64_t C, uint32_t* err) {
+  const int lane = threadIdx.x & 31;
+  uint64_t* st = P.unit_state;
+  if (g == first) {
+    if (lane == 0) st_relaxed(st + g, kStateInc | C);
+    return 0;
+  }
+  if (lane == 0) st_relaxed(st + g, kStateAgg | C);
+  uint64_t excl = 0;
+  int64_t j = static_cast<int64_t>(g) - 1;
+  const int64_t lo = static_cast<int64_t>(first);
+  const uint64_t t0 = static_cast<uint64_t>(clock64());
+  for (;;) {
+    uint64_t s[kLbPerLane];
+    lb_load(st, j, lo, lane, s);
+    bool has_inc = false, notready = false;
+    uint64_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kLbPerLane; ++k) {
+      if (!has_inc) {
+        const uint32_t flag = static_cast<uint32_t>(s[k] >> 62);
+        notready |= flag == 0u;
+        sum += s[k] & kStateValMask;
+        has_inc = flag == 2u;
+      }
+    }
+    const uint32_t inc = __ballot_sync(0xffffffffu, has_inc);
+    const uint32_t need = inc ? (((inc & (0u - inc)) << 1) - 1u) : 0xffffffffu;
+    if (__ballot_sync(0xffffffffu, notready) & need) {
+      bool go = true;
+      if (lane == 0) go = backoff_wait(P, t0);
+      if (!__shfl_sync(0xffffffffu, go, 0)) {
+        if (lane == 0) atomicOr(err, kErrTimeout);
+        break;
+      }
+      continue;
+    }
+    excl += warp_sum_u64((need >> lane) & 1u ? sum : 0ull);
+    if (inc) break;
+    j -= kLbSpan;
+  }
+  if (lane == 0) st_relaxed(st + g, kStateInc | ((excl + C) & kStateValMask));
+  return excl;
+}
+
+
 // Algorithm 1 (Sec. IV-B): the block's output [0, C) is produced through a
 // shared-memory window of `window` symbols.  A thread decodes its whole range
 // [o, o + c) into the window only when it fits; the first thread that does

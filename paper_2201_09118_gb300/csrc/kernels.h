@@ -27,6 +27,7 @@ struct LaunchShape {
   uint32_t grid;     // persistent blocks (0: full occupancy)
   uint32_t lut16;    // 1: the decode-and-write kernel uses 16-bit first-level entries
   uint32_t runs;     // 1: the count kernel takes several short codes per lookup (run table)
+  uint32_t decoder;  // 0 automatic, 1 two phases, 2 one pass (hd_config.decoder)
 };
 
 // Dynamic shared memory of the single-pass gap-array kernel.
@@ -88,6 +89,17 @@ size_t sync_smem_bytes(const LaunchShape& s);
 // per-subsequence scratch in global memory.
 cudaError_t launch_decode_single_pass(const DecodeParams& p, const LaunchShape& s, int num_sms,
                                       cudaStream_t stream);
+
+// One-pass gap-array decode of a single field with warp-sized tiles
+// (decode_warp.cu): s.threads / 32 warps per block, each warp decoding tiles of
+// 32 subsequences once into a column scratch of s.cmax symbols per lane,
+// offsets from a look-back over p.unit_state (one state per tile, zeroed with
+// p.ticket and p.abort_flag before the launch), Algorithm 1's window per warp.
+cudaError_t launch_decode_warp(const DecodeParams& p, const LaunchShape& s, int num_sms,
+                               cudaStream_t stream);
+
+// Dynamic shared memory of the one-pass decoder.
+size_t warp_decode_smem_bytes(const LaunchShape& s);
 
 // GPU encoder: symbol tiles of a stream of n symbols; per-tile code bits and
 // their scan (tile_off[tiles] = stream bits); then the stream and gap array.

@@ -9,8 +9,11 @@
 // max_batch) whose outputs fit the budget -- outputs are carved from one
 // device allocation of budget bytes -- and queues them as one hd_decode_batch
 // call.  Completion is observed with an event per slot; latency is measured
-// from submission to that observation.  The paper decodes one field per
-// launch; this loop is the serving counterpart of its batched decoder.
+// from submission to that observation.  A watchdog (watch.h) bounds the wait:
+// a batch still running after cfg.watchdog_us has its requests completed with
+// HD_ERR_TIMEOUT, while its slot and their output memory stay held until the
+// device work really ends.  The paper decodes one field per launch; this loop
+// is the serving counterpart of its batched decoder.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,6 +29,7 @@
 
 #include "arena.h"
 #include "hd.h"
+#include "watch.h"
 
 namespace {
 
@@ -50,9 +54,17 @@ struct Slot {
   hd_ctx* ctx = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  bool busy = false;
+  hd::SlotWatch watch;
   std::vector<uint64_t> tickets;
 };
+
+constexpr uint64_t kDefaultWatchdogUs = 10000000;  // 10 s
+
+uint64_t now_us() {
+  return static_cast<uint64_t>(
+      std::chrono::duration_cast<std::chrono::microseconds>(Clock::now().time_since_epoch())
+          .count());
+}
 
 }  // namespace
 
@@ -75,6 +87,9 @@ struct hd_server {
   size_t inflight = 0;
   bool stop = false;
   uint64_t submitted = 0, completed = 0, batches = 0;
+  uint64_t watchdog_us = 0;  // per-batch limit (0: none)
+  uint64_t retired = 0;      // timed-out batches whose work ended later
+  uint64_t stop_us = 0;      // when shutdown found only timed-out batches left
 };
 
 namespace {
@@ -89,22 +104,35 @@ int check_resident(const hd_field* f) {
   return HD_OK;
 }
 
-// Marks the requests of a finished (or failed) slot done.
-void finish_slot(hd_server* s, Slot& sl, const std::vector<int32_t>& st) {
+// Marks the requests of a finished (or failed) slot done.  With `hold` (the
+// batch timed out and may still be running) their output blocks move to the
+// slot's watch instead of staying with the requests, so releasing a request
+// cannot hand memory the GPU may still write to another one.
+void finish_requests(hd_server* s, Slot& sl, const std::vector<int32_t>& st, bool hold) {
   const auto now = Clock::now();
   for (size_t j = 0; j < sl.tickets.size(); ++j) {
     auto it = s->reqs.find(sl.tickets[j]);
     if (it == s->reqs.end()) continue;
-    it->second.status = st[j];
-    it->second.t_done = now;
-    it->second.state = State::kDone;
+    Request& r = it->second;
+    r.status = st[j];
+    r.t_done = now;
+    r.state = State::kDone;
+    if (hold && r.out_off != hd::Arena::kNone) {
+      sl.watch.hold(r.out_off);
+      r.out_off = hd::Arena::kNone;
+    }
     s->finished.push_back(sl.tickets[j]);
   }
   s->inflight -= sl.tickets.size();
   s->completed += sl.tickets.size();
   sl.tickets.clear();
-  sl.busy = false;
   s->cv_done.notify_all();
+}
+
+bool any_busy(const hd_server* s) {
+  for (const auto& sl : s->slots)
+    if (sl.watch.busy()) return true;
+  return false;
 }
 
 void serve_loop(hd_server* s) {
@@ -112,11 +140,24 @@ void serve_loop(hd_server* s) {
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
     bool progressed = false;
-    // completions
+    // completions, time-outs and retirements
     for (auto& sl : s->slots) {
-      if (!sl.busy) continue;
+      if (!sl.watch.busy()) continue;
       const cudaError_t q = cudaEventQuery(sl.done);
-      if (q == cudaErrorNotReady) continue;
+      const auto v = sl.watch.poll(q != cudaErrorNotReady, now_us());
+      if (v == hd::SlotWatch::Verdict::kWaiting) continue;
+      progressed = true;
+      if (v == hd::SlotWatch::Verdict::kTimedOut) {
+        finish_requests(s, sl, std::vector<int32_t>(sl.tickets.size(), HD_ERR_TIMEOUT), true);
+        continue;
+      }
+      if (q != cudaSuccess && q != cudaErrorNotReady) cudaGetLastError();
+      if (v == hd::SlotWatch::Verdict::kRetired) {
+        // the late batch's statuses were reported as time-outs already
+        for (size_t off : sl.watch.take_held()) s->arena.release(off);
+        ++s->retired;
+        continue;
+      }
       std::vector<int32_t> st(sl.tickets.size(), HD_ERR_CUDA);
       if (q == cudaSuccess) {
         lk.unlock();
@@ -126,15 +167,12 @@ void serve_loop(hd_server* s) {
           hd_batch_status(sl.ctx, st.data(), static_cast<uint32_t>(st.size()), sl.stream);
         }
         lk.lock();
-      } else {
-        cudaGetLastError();
       }
-      finish_slot(s, sl, st);
-      progressed = true;
+      finish_requests(s, sl, st, false);
     }
     // admissions: oldest requests first, while their outputs fit the budget
     for (auto& sl : s->slots) {
-      if (sl.busy || s->pending.empty()) continue;
+      if (sl.watch.busy() || s->pending.empty()) continue;
       std::vector<uint64_t> take;
       while (!s->pending.empty() && take.size() < s->cfg.max_batch) {
         Request& r = s->reqs[s->pending.front()];
@@ -156,7 +194,7 @@ void serve_loop(hd_server* s) {
         outs.push_back(reinterpret_cast<uint16_t*>(s->base + r.out_off));
       }
       sl.tickets = take;
-      sl.busy = true;
+      sl.watch.launch(now_us(), s->watchdog_us);
       s->inflight += take.size();
       s->batches += 1;
       lk.unlock();
@@ -169,7 +207,10 @@ void serve_loop(hd_server* s) {
       }
       if (rc == HD_OK && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) rc = HD_ERR_CUDA;
       lk.lock();
-      if (rc != HD_OK) finish_slot(s, sl, std::vector<int32_t>(take.size(), rc));
+      if (rc != HD_OK) {
+        finish_requests(s, sl, std::vector<int32_t>(take.size(), rc), false);
+        sl.watch.poll(true, now_us());  // nothing was queued: the slot is free again
+      }
       progressed = true;
     }
     if (s->stop && !s->pending.empty()) {
@@ -185,7 +226,13 @@ void serve_loop(hd_server* s) {
       s->pending.clear();
       s->cv_done.notify_all();
     }
-    if (s->stop && s->inflight == 0) break;
+    if (s->stop && s->inflight == 0) {
+      // timed-out batches still on the GPU keep their slots until they end,
+      // for one more watchdog period; after that they are abandoned
+      if (!any_busy(s)) break;
+      if (!s->stop_us) s->stop_us = now_us();
+      if (now_us() - s->stop_us > s->watchdog_us) break;
+    }
     if (progressed) continue;
     const uint64_t w = s->wake.load();
     if (s->inflight) {
@@ -193,10 +240,16 @@ void serve_loop(hd_server* s) {
       lk.unlock();
       for (int k = 0; k < 64 && s->wake.load() == w; ++k) {
         bool ready = false;
-        for (auto& sl : s->slots) ready |= sl.busy && cudaEventQuery(sl.done) != cudaErrorNotReady;
+        for (auto& sl : s->slots)
+          ready |= sl.watch.busy() && cudaEventQuery(sl.done) != cudaErrorNotReady;
         if (ready) break;
         std::this_thread::yield();
       }
+      lk.lock();
+    } else if (any_busy(s)) {
+      // only timed-out batches are left on the GPU: look again later
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(200));
       lk.lock();
     } else {
       s->cv_work.wait(lk, [&] { return s->wake.load() != w; });
@@ -228,6 +281,7 @@ int hd_serve_create(int device, const hd_serve_config* cfg, const hd_config* sha
   s->device = device;
   s->cfg = *cfg;
   if (!s->cfg.queue_cap) s->cfg.queue_cap = 1u << 20;
+  s->watchdog_us = cfg->watchdog_us ? cfg->watchdog_us : kDefaultWatchdogUs;
   int rc = HD_OK;
   if (cudaMalloc(&s->base, cfg->budget_bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -274,13 +328,20 @@ int hd_serve_destroy(hd_server* s) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(s->device);
+  bool abandoned = false;
   for (auto& sl : s->slots) {
+    if (sl.watch.busy()) {
+      // a timed-out batch that never ended: its context, stream and the
+      // output memory stay allocated rather than freed under running work
+      abandoned = true;
+      continue;
+    }
     if (sl.stream) cudaStreamSynchronize(sl.stream);
     if (sl.ctx) hd_ctx_destroy(sl.ctx);
     if (sl.stream) cudaStreamDestroy(sl.stream);
     if (sl.done) cudaEventDestroy(sl.done);
   }
-  if (s->base) cudaFree(s->base);
+  if (s->base && !abandoned) cudaFree(s->base);
   cudaSetDevice(prev);
   delete s;
   return HD_OK;
@@ -378,6 +439,10 @@ int hd_serve_stats(hd_server* s, hd_serve_stats_t* out) {
   out->budget_bytes = s->arena.capacity();
   out->used_bytes = s->arena.used();
   out->peak_bytes = s->arena.peak();
+  uint64_t held = 0;
+  for (const auto& sl : s->slots) held += sl.watch.timed_out() ? 1 : 0;
+  out->timed_out_batches = held;
+  out->retired_batches = s->retired;
   return HD_OK;
 }
 

@@ -92,6 +92,10 @@ __device__ void build_table(const FieldDesc& F, uint32_t K) {
     H->nused = s_nused;
     H->K = K;
     H->long0 = s_start[K + 1 <= 33 ? K + 1 : 33];
+    uint32_t lmin = 0;
+    for (int L = 32; L >= 1; --L)
+      if (cnt[L]) lmin = L;
+    H->minlen = lmin;
     for (int L = 0; L < 34; ++L) {
       H->end[L] = s_end[L];
       H->base[L] = s_base[L];

@@ -55,13 +55,13 @@ class hd_field(ctypes.Structure):
 class hd_config(ctypes.Structure):
     _fields_ = [("subseq_bits", ctypes.c_uint32), ("threads", ctypes.c_uint32),
                 ("window", ctypes.c_uint32), ("lut_bits", ctypes.c_uint32),
-                ("cr_classes", ctypes.c_uint32)]
+                ("cr_classes", ctypes.c_uint32), ("decoder", ctypes.c_uint32)]
 
 
 class hd_serve_config(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32),
                 ("max_batch", ctypes.c_uint32), ("queue_cap", ctypes.c_uint32),
-                ("direct", ctypes.c_uint32)]
+                ("direct", ctypes.c_uint32), ("watchdog_us", ctypes.c_uint32)]
 
 
 class hd_result(ctypes.Structure):
@@ -72,7 +72,8 @@ class hd_result(ctypes.Structure):
 class hd_serve_stats_t(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "completed", "batches", "pending",
                                                 "in_flight", "budget_bytes", "used_bytes",
-                                                "peak_bytes")]
+                                                "peak_bytes", "timed_out_batches",
+                                                "retired_batches")]
 
 
 class hd_lorenzo(ctypes.Structure):
@@ -131,6 +132,8 @@ _SIGS = {
     "hd_decode_host": ([_P, ctypes.POINTER(hd_field), _P, _P], ctypes.c_int),
     "hd_decode_static": ([ctypes.POINTER(hd_field), _P, _P], ctypes.c_int),
     "hd_profile": ([_P, ctypes.c_int], ctypes.c_int),
+    "hd_phase_times": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
+                       ctypes.c_int),
     "hd_kernel_time": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
                        ctypes.c_int),
     "hd_launch_count": ([_P], ctypes.c_uint64),
@@ -297,8 +300,10 @@ class Context:
         except Exception:
             pass
 
-    def set_config(self, subseq_bits=0, threads=0, window=0, lut_bits=0, cr_classes=0):
-        cfg = hd_config(subseq_bits, threads, window, lut_bits, cr_classes)
+    def set_config(self, subseq_bits=0, threads=0, window=0, lut_bits=0, cr_classes=0,
+                   decoder=0):
+        """decoder: 0 automatic, 1 two phases, 2 one pass (hd_config.decoder)."""
+        cfg = hd_config(subseq_bits, threads, window, lut_bits, cr_classes, decoder)
         _check("hd_set_config", self._lib.hd_set_config(self.handle, ctypes.byref(cfg)))
 
     def reset_config(self):
@@ -308,7 +313,7 @@ class Context:
         cfg = hd_config()
         _check("hd_get_config", self._lib.hd_get_config(self.handle, ctypes.byref(cfg)))
         return {"subseq_bits": cfg.subseq_bits, "threads": cfg.threads, "window": cfg.window,
-                "lut_bits": cfg.lut_bits, "cr_classes": cfg.cr_classes}
+                "lut_bits": cfg.lut_bits, "cr_classes": cfg.cr_classes, "decoder": cfg.decoder}
 
     def decode(self, field: DeviceField, out, stream=None) -> None:
         f = field.c_struct()
@@ -356,7 +361,7 @@ class Context:
         _check("hd_autotune", self._lib.hd_autotune(self.handle, arr, nf, ptrs,
                                                     _stream_handle(stream), ctypes.byref(cfg)))
         return {"subseq_bits": cfg.subseq_bits, "threads": cfg.threads, "window": cfg.window,
-                "lut_bits": cfg.lut_bits, "cr_classes": cfg.cr_classes}
+                "lut_bits": cfg.lut_bits, "cr_classes": cfg.cr_classes, "decoder": cfg.decoder}
 
     def graph_stats(self):
         cap = ctypes.c_uint64()
@@ -439,6 +444,15 @@ class Context:
                                                           ctypes.byref(n)))
         return ms.value, n.value
 
+    def phase_times(self):
+        """Per-phase ms of the profiled single-field decodes since the last
+        call (hd_phase_times): dict sync / count / index / write, plus decodes."""
+        ms = (ctypes.c_double * 4)()
+        n = ctypes.c_uint64()
+        _check("hd_phase_times", self._lib.hd_phase_times(self.handle, ms, ctypes.byref(n)))
+        return {"sync": ms[0], "count": ms[1], "index": ms[2], "write": ms[3],
+                "decodes": n.value}
+
     def launch_count(self) -> int:
         return int(self._lib.hd_launch_count(self.handle))
 
@@ -449,13 +463,15 @@ class Server:
 
     def __init__(self, device: int = 0, budget_bytes: int = 40 << 30, slots: int = 2,
                  max_batch: int = 64, queue_cap: int = 0, direct: bool = False,
-                 shape: Optional[dict] = None):
+                 shape: Optional[dict] = None, watchdog_us: int = 0):
         self._lib = load()
-        cfg = hd_serve_config(budget_bytes, slots, max_batch, queue_cap, 1 if direct else 0)
+        cfg = hd_serve_config(budget_bytes, slots, max_batch, queue_cap, 1 if direct else 0,
+                              watchdog_us)
         sh = None
         if shape:
             sh = hd_config(shape.get("subseq_bits", 0), shape.get("threads", 0),
-                           shape.get("window", 0), shape.get("lut_bits", 0))
+                           shape.get("window", 0), shape.get("lut_bits", 0),
+                           shape.get("cr_classes", 0), shape.get("decoder", 0))
         h = ctypes.c_void_p()
         _check("hd_serve_create", self._lib.hd_serve_create(
             device, ctypes.byref(cfg), ctypes.byref(sh) if sh is not None else None,

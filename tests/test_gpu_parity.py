@@ -88,17 +88,25 @@ def test_sync_points_equal_gap_array(ctx):
         assert np.all(got[nsub:] == 255)
 
 
+# strategy, decoder: gap arrays through the two-phase kernels (1) and the
+# one-pass kernel (2); self-synchronisation always runs two phases
+STRATEGIES = [(True, 1), (True, 2), (False, 0)]
+STRATEGY_IDS = ["gap-2phase", "gap-1pass", "selfsync"]
+
+
 @pytest.mark.parametrize("S", [64, 128, 256])
 @pytest.mark.parametrize("threads", [128, 256, 512])
-@pytest.mark.parametrize("with_gap", [True, False], ids=["gap", "selfsync"])
-def test_launch_shapes(ctx, S, threads, with_gap):
+@pytest.mark.parametrize("with_gap,decoder", STRATEGIES, ids=STRATEGY_IDS)
+def test_launch_shapes(ctx, S, threads, with_gap, decoder):
     x = synth.laplace_codes(200003, scale=30.0, seed=S + threads)
     c = oracle.compress(x, 1024, S=S)
     try:
         for window, K in ((S, 8), (1024, 11), (0, 12), (8192, 13), (0, 14), (2048, 15)):
             ctx.set_config(subseq_bits=S, threads=threads, window=max(window, S) if window else 0,
-                           lut_bits=K)
+                           lut_bits=K, decoder=decoder)
             check(ctx, c, with_gap)
+            if with_gap:
+                assert ctx.get_config()["decoder"] == decoder
     finally:
         ctx.reset_config()
 
@@ -149,11 +157,11 @@ def test_decoder_subsequence_multiple_of_stream(ctx, dec_S):
         ctx.reset_config()
 
 
-@pytest.mark.parametrize("with_gap", [True, False], ids=["gap", "selfsync"])
+@pytest.mark.parametrize("with_gap,decoder", STRATEGIES, ids=STRATEGY_IDS)
 @pytest.mark.parametrize("case", ["n1", "n2", "n3", "one_symbol", "two_symbols_skew",
                                   "fibonacci32", "alphabet256", "alphabet4096", "skew1e-2",
                                   "uniform_equal_lengths", "ragged"])
-def test_edge_cases(ctx, case, with_gap):
+def test_edge_cases(ctx, case, with_gap, decoder):
     rng = np.random.default_rng(zlib.crc32(case.encode()))
     A = 1024
     if case == "n1":
@@ -189,7 +197,11 @@ def test_edge_cases(ctx, case, with_gap):
     c = oracle.compress(x, A, S=128)
     if case == "fibonacci32":
         assert int(c["lengths"].max()) == 32
-    check(ctx, c, with_gap)
+    try:
+        ctx.set_config(decoder=decoder)
+        check(ctx, c, with_gap)
+    finally:
+        ctx.reset_config()
 
 
 def test_decode_host(ctx):
@@ -255,8 +267,16 @@ def test_batch_mixed_fields(ctx):
 # ---------------------------------------------------------------------------
 
 
-@pytest.mark.parametrize("with_gap", [True, False], ids=["gap", "selfsync"])
-def test_corrupt_streams(ctx, with_gap):
+@pytest.mark.parametrize("with_gap,decoder", STRATEGIES, ids=STRATEGY_IDS)
+def test_corrupt_streams(ctx, with_gap, decoder):
+    ctx.set_config(decoder=decoder)
+    try:
+        corrupt_streams(ctx, with_gap)
+    finally:
+        ctx.reset_config()
+
+
+def corrupt_streams(ctx, with_gap):
     from paper_2201_09118_gb300 import hd
     x = synth.laplace_codes(200000, scale=6.0, seed=13)
     c = oracle.compress(x, 1024, S=128)
@@ -331,14 +351,19 @@ def test_invalid_codebook_and_arguments(ctx):
     assert e.value.code == hd.HD_ERR_ARG
 
 
+@pytest.mark.parametrize("decoder", [1, 2], ids=["2phase", "1pass"])
 @pytest.mark.parametrize("shift", [1, 3, 7])
-def test_unaligned_output(ctx, shift):
+def test_unaligned_output(ctx, shift, decoder):
     x = synth.laplace_codes(99991, scale=3.0, seed=15)
     c = oracle.compress(x, 1024, S=128)
     f = dev_field(c)
     buf = torch.full((c["n"] + 32,), CANARY, dtype=torch.int32).to(torch.int16).cuda()
-    ctx.decode(f, buf[shift:])
-    assert ctx.status() == 0
+    ctx.set_config(decoder=decoder)
+    try:
+        ctx.decode(f, buf[shift:])
+        assert ctx.status() == 0
+    finally:
+        ctx.reset_config()
     r = buf.cpu().numpy().view(np.uint16)
     assert np.all(r[:shift] == np.uint16(CANARY))
     assert np.array_equal(r[shift:shift + c["n"]], x)
@@ -375,7 +400,7 @@ def test_full_512cube_in_the_benchmark_launch_shape(cube, with_gap):
     f = dev_field(c, with_gap)
     out = torch.full((c["n"] + 64,), CANARY, dtype=torch.int32).to(torch.int16).cuda()
     best = tctx.autotune([f], [out])
-    assert best["threads"] in (128, 256, 512)
+    assert best["threads"] in (128, 256, 512, 1024)
     out.fill_(CANARY - 65536)
     tctx.decode(f, out)
     assert tctx.status() == 0

@@ -168,3 +168,44 @@ def test_destroy_with_requests_waiting_for_memory(pool):
     t0 = time.time()
     srv.close()
     assert time.time() - t0 < 10
+
+
+def test_watchdog_times_out_batches_without_handing_out_their_memory(pool):
+    # a 1-microsecond limit: batches are (almost always) still on the GPU when
+    # the worker first looks, so their requests complete with HD_ERR_TIMEOUT
+    # and no output, while the slot and the output memory stay held until the
+    # work really ends; nothing hangs and the budget comes back in full
+    from paper_2201_09118_gb300 import hd
+    fields, alone, _ = pool
+    srv = hd.Server(0, budget_bytes=1 << 30, slots=2, max_batch=8, watchdog_us=1)
+    ids = [srv.register(f) for f in fields]
+    tickets = {srv.submit(ids[k % len(ids)]): k % len(ids) for k in range(48)}
+    got = collect(srv, tickets)
+    statuses = [res["status"] for res, _ in got.values()]
+    assert set(statuses) <= {hd.HD_OK, hd.HD_ERR_TIMEOUT}
+    assert statuses.count(hd.HD_ERR_TIMEOUT) > 0
+    for t, (res, out) in got.items():
+        if res["status"] == hd.HD_ERR_TIMEOUT:
+            assert res["d_out"] in (None, 0)
+        else:
+            assert torch.equal(out, alone[tickets[t]])
+    srv.drain()
+    t0 = time.time()
+    while True:  # timed-out batches retire once their work has ended
+        st = srv.stats()
+        if st["timed_out_batches"] == 0 and st["used_bytes"] == 0:
+            break
+        assert time.time() - t0 < 30, st
+        time.sleep(0.01)
+    assert st["retired_batches"] > 0
+    assert st["completed"] == st["submitted"] == 48
+    srv.close()
+    # the default limit: the same requests all decode
+    srv = hd.Server(0, budget_bytes=1 << 30, slots=2, max_batch=8)
+    ids = [srv.register(f) for f in fields]
+    tickets = {srv.submit(ids[k % len(ids)]): k % len(ids) for k in range(48)}
+    for t, (res, out) in collect(srv, tickets).items():
+        assert res["status"] == hd.HD_OK
+        assert torch.equal(out, alone[tickets[t]])
+    assert srv.stats()["timed_out_batches"] == 0
+    srv.close()

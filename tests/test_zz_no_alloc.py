@@ -71,3 +71,32 @@ def test_decode_static_rejects_oversized_field_before_gpu_work():
     rc = lib.hd_decode_static(ctypes.byref(f), ctypes.c_void_p(out.data_ptr()), None)
     assert rc == hd.HD_ERR_CAPACITY
     torch.cuda.synchronize()
+
+
+def test_decode_static_corrupt_call_then_clean_call():
+    # the error word lives in the shared fixed array: a call that fails must not
+    # leave its error bits to the next call on the same array
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_09118_gb300 import hd
+    lib = hd.load()
+    stream = torch.cuda.current_stream()
+    x = synth.laplace_codes(400_009, scale=6.0, seed=33)
+    c = oracle.compress(x, 1024, S=128)
+    enc = {"words": c["words"], "gap": c["gap"], "nbits": c["nbits"], "subseq_bits": 128}
+    good = hd.DeviceField.upload(enc, c["lengths"], c["n"])
+    bad_gap = c["gap"].copy()
+    bad_gap[len(bad_gap) // 3] = 200  # no codeword starts 200 bits into a subsequence
+    bad = hd.DeviceField.upload(dict(enc, gap=bad_gap), c["lengths"], c["n"])
+    n = c["n"]
+    for field, want in ((bad, hd.HD_ERR_CORRUPT), (good, hd.HD_OK), (bad, hd.HD_ERR_CORRUPT),
+                        (good, hd.HD_OK)):
+        out = torch.full((n + 16,), CANARY, dtype=torch.int32).to(torch.int16).cuda()
+        cf = field.c_struct()
+        rc = lib.hd_decode_static(ctypes.byref(cf), ctypes.c_void_p(out.data_ptr()),
+                                  ctypes.c_void_p(stream.cuda_stream))
+        assert rc == want
+        got = out.cpu().numpy().view(np.uint16)
+        assert np.all(got[n:] == np.uint16(CANARY))
+        if want == hd.HD_OK:
+            assert np.array_equal(got[:n], x)
