@@ -126,7 +126,7 @@ typedef struct hd_config {
                            field's S */
   uint32_t threads;     /* threads per block: 128, 256, 512 (two phases: one
                            subsequence per thread, a tile per block); one pass
-                           also 1024 (a tile per warp) */
+                           also 768 and 1024 (a tile per warp) */
   uint32_t window;      /* shared-memory output window in symbols (Alg. 1 buffer);
                            0 = sized from the field's mean code length */
   uint32_t lut_bits;    /* first-level decode-table index bits, 8 .. 15 (0 = 13
@@ -412,6 +412,15 @@ int hd_encode_device(hd_ctx* ctx, const uint16_t* d_codes, uint64_t n, const uin
                      uint32_t alphabet, uint32_t subseq_bits, uint32_t* d_words,
                      uint64_t words_cap, uint8_t* d_gap, uint64_t gap_cap, hd_stream_info* info,
                      void* stream);
+
+/* Limit on each device-side wait of the one-pass decoder (a tile waiting in
+ * its look-back for the counts of the tiles before it), in SM clock cycles;
+ * 0 restores the default of about 2 s.  A wait that reaches the limit gives
+ * up, every later wait of that decode returns at once, the decode still
+ * writes nothing outside its output, and hd_status reports HD_ERR_TIMEOUT;
+ * the context stays usable.  A very short limit makes waits give up on
+ * purpose, which is how failure detection is tested without hanging a GPU. */
+int hd_set_wait_limit(hd_ctx* ctx, uint64_t cycles);
 
 /* Kernel timing: when enabled, the context records CUDA events around every
  * main decode kernel it launches.  hd_kernel_time waits for them and returns

@@ -63,6 +63,7 @@ struct hd_ctx {
   std::vector<cudaEvent_t> pipe_ev;
   uint64_t* pin_ends = nullptr;      // host-mapped: chunk ends written by the tile scan
   uint64_t* pin_ends_dev = nullptr;  // the same memory as the device sees it
+  uint64_t wait_limit = 0;           // one-pass decoder: cycles per look-back wait (0: default)
   // autotuner results: batch class -> launch shape
   std::map<TuneKey, hd_config> tuned;
   // Lorenzo reconstruction: its workspace (error word first), whether its
@@ -488,7 +489,7 @@ uint32_t one_pass_cmax(uint32_t S, double bits_per) {
 }
 
 // Queues a one-pass decode of one gap-array field (decode_warp.cu).
-// Workspace: error word | ticket, abort flag | one look-back state per tile
+// Workspace: error word | abort flag | one look-back state per tile
 // (the three cleared by the table kernel) | decode table.
 int queue_decode_one_pass(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::LaunchShape& shape,
                           cudaStream_t st) {
@@ -506,10 +507,14 @@ int queue_decode_one_pass(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::La
   const size_t budget = static_cast<size_t>(c->max_smem) - 2048;
   const bool fixed_threads = s.threads != 0;
   if (!fixed_threads) {
-    s.threads = 1024;
-    while (s.threads > 128 && hd::warp_decode_smem_bytes(s) > budget) s.threads >>= 1;
+    // the most warps per block that shared memory holds
+    for (uint32_t b : {1024u, 768u, 512u, 256u, 128u}) {
+      s.threads = b;
+      if (hd::warp_decode_smem_bytes(s) <= budget) break;
+    }
   }
-  if (s.threads != 128 && s.threads != 256 && s.threads != 512 && s.threads != 1024)
+  if (s.threads != 128 && s.threads != 256 && s.threads != 512 && s.threads != 768 &&
+      s.threads != 1024)
     return HD_ERR_ARG;
   // the column is an optimisation (overflowing lanes decode again), so it
   // shrinks to fit shared memory
@@ -548,7 +553,7 @@ int queue_decode_one_pass(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::La
   dp.unit_state = reinterpret_cast<uint64_t*>(ws + st_off);
   dp.ticket = reinterpret_cast<uint32_t*>(ws + tk_off);
   dp.abort_flag = reinterpret_cast<uint32_t*>(ws + tk_off) + 1;
-  dp.timeout_cycles = kLookbackTimeoutCycles;
+  dp.timeout_cycles = c->wait_limit ? c->wait_limit : kLookbackTimeoutCycles;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->profile) {
     e0 = next_event(c);
@@ -1134,7 +1139,7 @@ int hd_set_config(hd_ctx* c, const hd_config* cfg) {
   if (cfg->subseq_bits && !valid_S(cfg->subseq_bits) && cfg->subseq_bits != 512) return HD_ERR_ARG;
   if (cfg->decoder > 2) return HD_ERR_ARG;
   if (cfg->threads && cfg->threads != 128 && cfg->threads != 256 && cfg->threads != 512 &&
-      !(cfg->threads == 1024 && cfg->decoder == 2))
+      !((cfg->threads == 768 || cfg->threads == 1024) && cfg->decoder == 2))
     return HD_ERR_ARG;
   if (cfg->lut_bits && (cfg->lut_bits < 8 || cfg->lut_bits > 15)) return HD_ERR_ARG;
   if (cfg->cr_classes && (cfg->cr_classes < 2 || cfg->cr_classes > 32)) return HD_ERR_ARG;
@@ -1279,7 +1284,7 @@ int hd_autotune(hd_ctx* c, const hd_field* fs, uint32_t nf, uint16_t* const* d_o
       const uint32_t i = idx[0];
       for (uint32_t S : S_list) {
         if (S < 128 || S % maxS) continue;
-        for (uint32_t B : {512u, 1024u}) {
+        for (uint32_t B : {256u, 512u, 768u}) {
           for (uint32_t K : {12u, 13u, 14u}) {
             c->cfg = hd_config{S, B, 0, K, 0, 2};
             const hd::LaunchShape sh = group_shape(c, fs, idx, true);
@@ -1794,6 +1799,13 @@ int hd_decompress_device(hd_ctx* c, const hd_field* f, const hd_lorenzo* L, floa
   c->err_count = err_words;
   c->err_off = err_off;
   return rc;
+}
+
+int hd_set_wait_limit(hd_ctx* c, uint64_t cycles) {
+  if (!c) return HD_ERR_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->wait_limit = cycles;
+  return HD_OK;
 }
 
 int hd_profile(hd_ctx* c, int enable) {

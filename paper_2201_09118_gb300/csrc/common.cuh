@@ -30,6 +30,13 @@ struct TableHeader {
   uint32_t base[34]; // start[L] - first[L] (mod 2^32): rank = (w >> (32-L)) + base[L]
   uint32_t long0;    // rank of the first code longer than K (codes sorted by length)
   uint32_t minlen;   // shortest code length in use (0 if no symbol is used)
+  // second-level tables of the 16-bit table (table_sub_off): first-level
+  // prefixes sub_p0 .. sub_p0 + nsub - 1 hold codes longer than K bits, and
+  // sub-table s resolves, by the sub_bits bits after the prefix, every code
+  // of prefix sub_p0 + s that is at most K + sub_bits long
+  uint32_t sub_bits;
+  uint32_t nsub;
+  uint32_t sub_p0;
 };
 static_assert(sizeof(TableHeader) <= kTableHeaderBytes, "table header too large");
 
@@ -69,6 +76,15 @@ __host__ __device__ constexpr uint64_t table_len8_off(uint32_t K, uint32_t A) {
 // longer than K bits (or is no code).
 __host__ __device__ constexpr uint64_t table_run8_off(uint32_t K, uint32_t A) {
   return table_len8_off(K, A) + (static_cast<uint64_t>(1) << K);
+}
+// Second-level tables (uint16[kSubCap] after the run table, 16-byte aligned):
+// entry (s << sub_bits) | q is ((L - K) << 12) | symbol for the code of length
+// L <= K + sub_bits whose first K + sub_bits bits are prefix sub_p0 + s then q,
+// else 0 (a longer code, or no code: the limits are walked).
+constexpr uint32_t kSubCap = 4096;
+__host__ __device__ constexpr uint64_t table_sub_off(uint32_t K, uint32_t A) {
+  return (table_run8_off(K, A) + (static_cast<uint64_t>(1) << K) + 15) &
+         ~static_cast<uint64_t>(15);
 }
 __host__ __device__ constexpr bool lut16_usable(uint32_t K, uint32_t A) {
   return A <= 4096 && K <= 15;

@@ -229,6 +229,7 @@ __device__ __forceinline__ uint64_t lookback_counts(const DecodeParams& P, uint6
   int64_t j = static_cast<int64_t>(g) - 1;
   const int64_t lo = static_cast<int64_t>(first);
   const uint64_t t0 = static_cast<uint64_t>(clock64());
+  uint32_t nap = 32;  // ns between re-reads of predecessors not yet counted
   for (;;) {
     uint64_t s[kLbPerLane];
     lb_load(st, j, lo, lane, s);
@@ -252,6 +253,9 @@ __device__ __forceinline__ uint64_t lookback_counts(const DecodeParams& P, uint6
         if (lane == 0) atomicOr(err, kErrTimeout);
         break;
       }
+      // leave the issue slots to the warps that are decoding
+      __nanosleep(nap);
+      nap = nap < 1024 ? 2 * nap : nap;
       continue;
     }
     excl += warp_sum_u64((need >> lane) & 1u ? sum : 0ull);

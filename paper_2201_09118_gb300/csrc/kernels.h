@@ -91,10 +91,11 @@ cudaError_t launch_decode_single_pass(const DecodeParams& p, const LaunchShape& 
                                       cudaStream_t stream);
 
 // One-pass gap-array decode of a single field with warp-sized tiles
-// (decode_warp.cu): s.threads / 32 warps per block, each warp decoding tiles of
-// 32 subsequences once into a column scratch of s.cmax symbols per lane,
-// offsets from a look-back over p.unit_state (one state per tile, zeroed with
-// p.ticket and p.abort_flag before the launch), Algorithm 1's window per warp.
+// (decode_warp.cu): s.threads / 32 warps per block in a cooperative launch,
+// each warp decoding tiles of 32 subsequences (round-robin over the grid's
+// warps) once into a column scratch of s.cmax symbols per lane, offsets from a
+// look-back over p.unit_state (one state per tile, zeroed with p.abort_flag
+// before the launch), Algorithm 1's window per warp.
 cudaError_t launch_decode_warp(const DecodeParams& p, const LaunchShape& s, int num_sms,
                                cudaStream_t stream);
 

@@ -96,6 +96,9 @@ __device__ void build_table(const FieldDesc& F, uint32_t K) {
     for (int L = 32; L >= 1; --L)
       if (cnt[L]) lmin = L;
     H->minlen = lmin;
+    H->sub_bits = 0;
+    H->nsub = 0;
+    H->sub_p0 = 0;
     for (int L = 0; L < 34; ++L) {
       H->end[L] = s_end[L];
       H->base[L] = s_base[L];
@@ -170,6 +173,44 @@ __device__ void build_table(const FieldDesc& F, uint32_t K) {
     len8[p] = static_cast<uint8_t>(e8);
     run8[p] = static_cast<uint8_t>(r8);
   }
+
+  // Second-level tables of the 16-bit table.  Canonical codes longer than K
+  // bits are the windows from end[K] on, so their prefixes are consecutive:
+  // [end[K] >> (32-K), ceil(end[maxlen] / 2^(32-K))).  Each gets sub_bits more
+  // bits (as many as the longest code needs, at most 8, and as the kSubCap
+  // entries allow); the most probable long codes come first.
+  __shared__ uint32_t s_sub[3];  // sub_bits, nsub, sub_p0
+  if (t == 0) {
+    uint32_t kb = 0, ns = 0, p0 = 0;
+    if (with16 && maxlen > K) {
+      const uint32_t sh = 32 - K;
+      p0 = static_cast<uint32_t>(s_end[K] >> sh);
+      const uint64_t p1 = (s_end[maxlen] + (1ull << sh) - 1) >> sh;
+      kb = maxlen - K < 8 ? maxlen - K : 8;
+      const uint64_t nlong = p1 > p0 ? p1 - p0 : 0;
+      ns = static_cast<uint32_t>(nlong < (kSubCap >> kb) ? nlong : (kSubCap >> kb));
+    }
+    s_sub[0] = kb;
+    s_sub[1] = ns;
+    s_sub[2] = p0;
+    H->sub_bits = kb;
+    H->nsub = ns;
+    H->sub_p0 = p0;
+  }
+  __syncthreads();
+  const uint32_t kb = s_sub[0], ns = s_sub[1], p0 = s_sub[2];
+  uint16_t* sub = reinterpret_cast<uint16_t*>(tb + table_sub_off(K, A));
+  for (uint32_t idx = t; idx < (ns << kb); idx += kPrepThreads) {
+    const uint32_t w = ((p0 + (idx >> kb)) << (32 - K)) | ((idx & ((1u << kb) - 1u)) << (32 - K - kb));
+    uint32_t L = K + 1;
+    while (L <= maxlen && static_cast<uint64_t>(w) >= s_end[L]) ++L;
+    uint16_t x = 0;
+    if (L <= K + kb && L <= maxlen) {
+      const uint32_t rank = (w >> (32 - L)) + s_base[L];
+      x = static_cast<uint16_t>(((L - K) << 12) | (sorted[rank] & 0xFFFu));
+    }
+    sub[idx] = x;
+  }
 }
 
 __global__ void __launch_bounds__(kPrepThreads) k_prepare(const __grid_constant__ PrepParams P) {
@@ -202,7 +243,7 @@ cudaError_t launch_prepare(const PrepParams& p, cudaStream_t stream) {
 }
 
 size_t table_bytes(uint32_t K, uint32_t alphabet) {
-  const size_t b = table_run8_off(K, alphabet) + (static_cast<size_t>(1) << K);
+  const size_t b = table_sub_off(K, alphabet) + 2 * static_cast<size_t>(kSubCap);
   return (b + 255) & ~static_cast<size_t>(255);
 }
 

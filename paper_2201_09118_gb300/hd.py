@@ -134,6 +134,7 @@ _SIGS = {
     "hd_profile": ([_P, ctypes.c_int], ctypes.c_int),
     "hd_phase_times": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
                        ctypes.c_int),
+    "hd_set_wait_limit": ([_P, ctypes.c_uint64], ctypes.c_int),
     "hd_kernel_time": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
                        ctypes.c_int),
     "hd_launch_count": ([_P], ctypes.c_uint64),
@@ -443,6 +444,10 @@ class Context:
         _check("hd_kernel_time", self._lib.hd_kernel_time(self.handle, ctypes.byref(ms),
                                                           ctypes.byref(n)))
         return ms.value, n.value
+
+    def set_wait_limit(self, cycles: int) -> None:
+        """Per-wait limit of the one-pass decoder's look-back (SM cycles; 0 = default)."""
+        _check("hd_set_wait_limit", self._lib.hd_set_wait_limit(self.handle, cycles))
 
     def phase_times(self):
         """Per-phase ms of the profiled single-field decodes since the last

@@ -61,7 +61,7 @@ def check(ctx, c, **cfg):
 
 
 @pytest.mark.parametrize("S", [128, 256, 512])
-@pytest.mark.parametrize("threads", [128, 256, 512, 1024])
+@pytest.mark.parametrize("threads", [128, 256, 512, 768, 1024])
 def test_warps_per_block_and_subsequence_bits(ctx, S, threads):
     # 331,337 codes at ~4.3 bits: tiles of 32 subsequences with a ragged last
     # tile (nsub not a multiple of 32, nbits not a multiple of S)
@@ -135,3 +135,28 @@ def test_full_512cube_one_pass(ctx):
         assert st == 0
         assert np.array_equal(res[:c["n"]], x)
         assert np.all(res[c["n"]:] == np.uint16(CANARY))
+
+
+def test_lookback_wait_limit_reports_timeout_and_context_stays_usable(ctx):
+    # failure detection without hanging the GPU: a one-cycle limit makes every
+    # look-back wait that finds a predecessor not yet counted give up; the
+    # decode reports HD_ERR_TIMEOUT, writes nothing past its output, and the
+    # next decode with the default limit is exact
+    from paper_2201_09118_gb300 import hd
+    x = synth.laplace_codes(1 << 23, scale=20.0, seed=71)
+    c = oracle.compress(x, 1024, S=128)
+    statuses = []
+    try:
+        ctx.set_wait_limit(1)
+        for _ in range(6):
+            st, res = decode(ctx, c)
+            statuses.append(st)
+            assert st in (hd.HD_OK, hd.HD_ERR_TIMEOUT)
+            assert np.all(res[c["n"]:] == np.uint16(CANARY))
+            if st == hd.HD_OK:
+                assert np.array_equal(res[:c["n"]], x)
+    finally:
+        ctx.set_wait_limit(0)
+    assert hd.HD_ERR_TIMEOUT in statuses
+    st, res = decode(ctx, c)
+    assert st == hd.HD_OK and np.array_equal(res[:c["n"]], x)
