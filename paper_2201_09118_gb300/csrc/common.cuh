@@ -171,6 +171,10 @@ struct DecodeParams {
   uint64_t n_out;
   const int32_t* out_corr;  // exclusive prefix of (residue + radius) over the outliers [n_out + 1]
   uint32_t* verr;           // kErrOutlier
+  // fields of short codes: where the shortest code has 1 bit (canonically
+  // the bit 0), a run of zero bits at a codeword boundary is a run of that
+  // code's symbol, counted and written as a whole
+  uint32_t zero_runs;
 };
 
 struct PrepParams {

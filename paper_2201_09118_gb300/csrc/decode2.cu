@@ -61,6 +61,18 @@ __device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* s_warp) {
   return tot;
 }
 
+// dst[0 .. z) = v (dst 2-byte aligned): 32-bit stores where aligned.
+__device__ __forceinline__ void fill_u16(uint16_t* dst, uint32_t z, uint32_t v) {
+  uint32_t k = 0;
+  if ((reinterpret_cast<uintptr_t>(dst) & 2u) && z) {
+    dst[0] = static_cast<uint16_t>(v);
+    k = 1;
+  }
+  const uint32_t v2 = (v & 0xFFFFu) * 0x10001u;
+  for (; k + 2 <= z; k += 2) *reinterpret_cast<uint32_t*>(dst + k) = v2;
+  if (k < z) dst[k] = static_cast<uint16_t>(v);
+}
+
 // What a thread needs of its subsequence of one tile, loaded ahead.
 template <int S>
 struct TileIn {
@@ -120,6 +132,7 @@ __global__ void __launch_bounds__(B, count_min_blocks<B>())
   __shared__ uint32_t s_base[34];
   __shared__ uint32_t s_meta[3];
   __shared__ uint32_t s_warp[B / 32];
+  __shared__ uint32_t s_lmin;
 
   const int t = threadIdx.x;
   uint32_t* col = s_bits + t;
@@ -148,6 +161,7 @@ __global__ void __launch_bounds__(B, count_min_blocks<B>())
     if (fi != cur_field) {
       __syncthreads();
       load_table(F.table, P.K, F.alphabet, kKind, s_lut, s_end, s_base, s_meta, B);
+      if (t == 0) s_lmin = F.table->minlen;
       cur_field = fi;
       __syncthreads();
     }
@@ -166,6 +180,7 @@ __global__ void __launch_bounds__(B, count_min_blocks<B>())
       }
       bool bad = false;
       const uint8_t* run8 = s_lut + (1u << P.K);
+      const bool zr = RUNS && P.zero_runs && s_lmin == 1;
       while (p < end) {
         if constexpr (kSums) {
           uint32_t sym;
@@ -176,7 +191,14 @@ __global__ void __launch_bounds__(B, count_min_blocks<B>())
           // several short codes per lookup when they all start before `end`
           const uint32_t w = peek<B>(col, p);
           const uint32_t r = run8[w >> T.shift];
-          if (r && p + (r & 15u) <= end) {
+          if (zr && !(w >> 31)) {
+            // a run of the 1-bit code 0: as many codes as zero bits, up to
+            // the end of the subsequence
+            uint32_t z = w ? __clz(w) : 32u;
+            z = min(z, end - p);
+            p += z;
+            c += z;
+          } else if (r && p + (r & 15u) <= end) {
             p += r & 15u;
             c += r >> 4;
           } else {
@@ -254,6 +276,7 @@ __global__ void __launch_bounds__(B, write_min_blocks<B>())
   __shared__ uint32_t s_flush_end;
   __shared__ uint64_t s_vtile[3];  // values: q before the tile, its outlier range
   __shared__ int32_t s_vw[2 * 32];
+  __shared__ uint32_t s_lmin, s_sym0;  // shortest code length, symbol of the first code
 
   const int t = threadIdx.x;
   uint32_t* col = s_bits + t;
@@ -295,6 +318,11 @@ __global__ void __launch_bounds__(B, write_min_blocks<B>())
       __syncthreads();
       load_table(F.table, P.K, F.alphabet, kKind, s_lut, s_end, s_base, s_meta, B, s_long,
                  P.long_cap);
+      if (t == 0) {
+        s_lmin = F.table->minlen;
+        s_sym0 = reinterpret_cast<const uint16_t*>(reinterpret_cast<const char*>(F.table) +
+                                                   table_sorted_off(P.K))[0];
+      }
       cur_field = fi;
       __syncthreads();
     }
@@ -311,10 +339,30 @@ __global__ void __launch_bounds__(B, write_min_blocks<B>())
     const uint32_t o = block_excl_scan<B>(c, s_warp, &C);
     const uint64_t base = s_tile_base;
     if (t == 0 && tl + 1 == F.nunits && base + C != F.n) atomicOr(F.err, kErrCount);
+    const bool zr = P.zero_runs && s_lmin == 1;
+    const uint32_t sym0 = s_sym0;
     auto decode = [&](uint16_t* dst) {
                       uint32_t p = gp;
                       bool bad = false;
                       uint32_t j = 0;
+                      if (zr) {
+                        // runs of the 1-bit code 0 go out whole, the other
+                        // codes one lookup each
+                        while (j < c) {
+                          const uint32_t w = peek<B>(col, p);
+                          if (!(w >> 31)) {
+                            uint32_t z = w ? __clz(w) : 32u;
+                            z = min(z, c - j);
+                            fill_u16(dst + j, z, sym0);
+                            j += z;
+                            p += z;
+                          } else {
+                            uint32_t s0;
+                            p += code_sym_t<E>(T, w, s0, bad);
+                            dst[j++] = static_cast<uint16_t>(s0);
+                          }
+                        }
+                      }
                       for (; j + 1 < c; j += 2) {
                         uint32_t s0, s1;
                         p += code_sym_t<E>(T, peek<B>(col, p), s0, bad);

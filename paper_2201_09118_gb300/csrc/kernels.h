@@ -26,7 +26,8 @@ struct LaunchShape {
   uint32_t long_cap; // symbols of long codes kept in shared memory
   uint32_t grid;     // persistent blocks (0: full occupancy)
   uint32_t lut16;    // 1: the decode-and-write kernel uses 16-bit first-level entries
-  uint32_t runs;     // 1: the count kernel takes several short codes per lookup (run table)
+  uint32_t runs;     // bit 0: the count kernel takes several short codes per lookup (run
+                     // table); bit 1: runs of a 1-bit code are counted and written whole
   uint32_t decoder;  // 0 automatic, 1 two phases, 2 one pass (hd_config.decoder)
 };
 

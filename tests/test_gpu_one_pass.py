@@ -160,3 +160,44 @@ def test_lookback_wait_limit_reports_timeout_and_context_stays_usable(ctx):
     assert hd.HD_ERR_TIMEOUT in statuses
     st, res = decode(ctx, c)
     assert st == hd.HD_OK and np.array_equal(res[:c["n"]], x)
+
+
+@pytest.fixture(scope="module")
+def cube128():
+    # the 3D workload's generator at 128^3: codes of 8 to 19 bits, so the
+    # fixed-step decode loop and the second-level tables (codes longer than
+    # the first-level table) run
+    x = synth.field3d_codes(128, rel_eb=1e-4, noise=0.01, seed=1001)
+    c = oracle.compress(x, 1024, S=128)
+    assert int(c["lengths"][c["lengths"] > 0].min()) >= 8
+    return x, c
+
+
+@pytest.mark.parametrize("S", [128, 256, 512])
+@pytest.mark.parametrize("threads", [256, 512, 768, 1024])
+@pytest.mark.parametrize("K", [11, 13, 14])
+def test_long_codes_fixed_steps_and_second_level_tables(ctx, cube128, S, threads, K):
+    x, c = cube128
+    st, res = decode(ctx, c, subseq_bits=S, threads=threads, lut_bits=K)
+    assert st == 0
+    assert np.array_equal(res[:c["n"]], x)
+    assert np.all(res[c["n"]:] == np.uint16(CANARY))
+
+
+def test_wrong_gap_entries_of_long_code_streams(ctx, cube128):
+    # a wrong entry at a decoder subsequence's start is caught by the end
+    # check of the subsequence before it; an entry a wider decoder subsequence
+    # skips changes nothing; nothing is written past the output
+    from paper_2201_09118_gb300 import hd
+    x, c = cube128
+    for S, k, bad in ((128, 1001, lambda v: v ^ 1), (256, 2 * 2002, lambda v: 31 - v),
+                      (512, 4 * 3003, lambda v: (v + 3) % 32)):
+        g = c["gap"].copy()
+        g[k] = bad(int(g[k]))
+        st, res = decode(ctx, dict(c, gap=g), subseq_bits=S)
+        assert st == hd.HD_ERR_CORRUPT
+        assert np.all(res[c["n"]:] == np.uint16(CANARY))
+    g = c["gap"].copy()
+    g[4 * 1234 + 2] ^= 1
+    st, res = decode(ctx, dict(c, gap=g), subseq_bits=512)
+    assert st == hd.HD_OK and np.array_equal(res[:c["n"]], x)
