@@ -89,6 +89,7 @@ constexpr double kRunsBelowBits = 4.0;  // mean code length below which counting
 // 1.87 bits, whose runs are short)
 constexpr double kZeroRunsBelowBits = 1.25;
 constexpr uint32_t kDefaultK16 = 13;
+constexpr uint32_t kTableSlices = 16;  // blocks building a single field's decode table
 constexpr uint32_t kDefaultK = 12;
 
 struct DeviceGuard {
@@ -366,7 +367,9 @@ void make_params(const std::vector<FieldDesc>& descs, char* ws, const Layout& L,
   pp.fields = reinterpret_cast<const FieldDesc*>(ws + L.desc);
   pp.hdr = dyn ? reinterpret_cast<const hd::LaunchHeader*>(ws + L.hdr) : nullptr;
   pp.nfields = nf_param;
-  pp.table_blocks = std::min<uint32_t>(nf_param, 1024);
+  // a lone field's table is built by several blocks
+  pp.slices = nf_param == 1 ? kTableSlices : 1u;
+  pp.table_blocks = std::min<uint32_t>(nf_param * pp.slices, 1024);
   pp.K = s.K;
   pp.zero_ptr = reinterpret_cast<uint4*>(ws);
   pp.zero_vec = L.zero / 16;
@@ -541,7 +544,8 @@ int queue_decode_one_pass(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::La
   hd::PrepParams pp{};
   pp.f0 = d;
   pp.nfields = 1;
-  pp.table_blocks = 1;
+  pp.slices = kTableSlices;
+  pp.table_blocks = kTableSlices;
   pp.K = s.K;
   pp.zero_ptr = reinterpret_cast<uint4*>(ws);
   pp.zero_vec = zero / 16;

@@ -183,6 +183,7 @@ struct PrepParams {
   const LaunchHeader* hdr;  // as in DecodeParams
   uint32_t nfields;         // field count, or the capacity when hdr != NULL
   uint32_t table_blocks;    // blocks that build tables (each loops over fields)
+  uint32_t slices;          // blocks per field table (0 = 1): each fills 1/slices of the entries
   uint32_t K;
   uint4* zero_ptr;          // region cleared before the decode kernel
   uint64_t zero_vec;        // its size in 16-byte vectors

@@ -21,8 +21,11 @@ __device__ __forceinline__ const FieldDesc& field_at(const PrepParams& p, bool s
   return single ? p.f0 : p.fields[i];
 }
 
-// One block builds the table of one field.
-__device__ void build_table(const FieldDesc& F, uint32_t K) {
+// Block `sl` of `nsl` builds the table of one field: every block computes the
+// header and the sorted symbols (the same values), and fills entries
+// sl*kPrepThreads + t + k*nsl*kPrepThreads of the first- and second-level
+// tables.
+__device__ void build_table(const FieldDesc& F, uint32_t K, uint32_t sl, uint32_t nsl) {
   __shared__ uint32_t cnt[34];
   __shared__ uint32_t s_maxlen, s_bad, s_nused;
   __shared__ uint64_t s_end[34];
@@ -134,7 +137,7 @@ __device__ void build_table(const FieldDesc& F, uint32_t K) {
 
   // First-level table: entry p covers all windows whose top K bits equal p.
   const uint32_t maxlen = s_maxlen;
-  for (uint32_t p = t; p < (1u << K); p += kPrepThreads) {
+  for (uint32_t p = sl * kPrepThreads + t; p < (1u << K); p += nsl * kPrepThreads) {
     const uint32_t w = p << (32 - K);
     uint32_t L = 1;
     while (L <= 32 && static_cast<uint64_t>(w) >= s_end[L]) ++L;
@@ -200,7 +203,7 @@ __device__ void build_table(const FieldDesc& F, uint32_t K) {
   __syncthreads();
   const uint32_t kb = s_sub[0], ns = s_sub[1], p0 = s_sub[2];
   uint16_t* sub = reinterpret_cast<uint16_t*>(tb + table_sub_off(K, A));
-  for (uint32_t idx = t; idx < (ns << kb); idx += kPrepThreads) {
+  for (uint32_t idx = sl * kPrepThreads + t; idx < (ns << kb); idx += nsl * kPrepThreads) {
     const uint32_t w = ((p0 + (idx >> kb)) << (32 - K)) | ((idx & ((1u << kb) - 1u)) << (32 - K - kb));
     uint32_t L = K + 1;
     while (L <= maxlen && static_cast<uint64_t>(w) >= s_end[L]) ++L;
@@ -218,9 +221,10 @@ __global__ void __launch_bounds__(kPrepThreads) k_prepare(const __grid_constant_
   if (b < P.table_blocks) {
     const uint32_t nf = P.hdr ? P.hdr->nfields : P.nfields;
     const bool single = !P.hdr && P.nfields == 1;
-    for (uint32_t f = b; f < nf; f += P.table_blocks) {
+    const uint32_t nsl = P.slices ? P.slices : 1u;
+    for (uint32_t x = b; x < nf * nsl; x += P.table_blocks) {
       __syncthreads();  // the previous field's shared state is no longer read
-      build_table(field_at(P, single, f), P.K);
+      build_table(field_at(P, single, x / nsl), P.K, x % nsl, nsl);
     }
     return;
   }
