@@ -214,6 +214,15 @@ int hd_batch_status(hd_ctx* ctx, int32_t* status, uint32_t nf, void* stream);
 int hd_autotune(hd_ctx* ctx, const hd_field* fs, uint32_t nf, uint16_t* const* d_outs,
                 void* stream, hd_config* best);
 
+/* Keeps the autotuner's choices across processes: hd_autotune_save writes
+ * every batch class this context has tuned, with the device's name, to the
+ * text file `path` (replacing it); hd_autotune_load reads such a file and
+ * takes the entries of the same device name into this context, as if
+ * hd_autotune had chosen them (*loaded = their number).  HD_ERR_ARG for a
+ * file that cannot be opened or is not such a file (nothing is loaded then). */
+int hd_autotune_save(hd_ctx* ctx, const char* path);
+int hd_autotune_load(hd_ctx* ctx, const char* path, uint32_t* loaded);
+
 /* Graph statistics of a context: graphs captured since creation and graphs
  * currently cached. */
 int hd_graph_stats(hd_ctx* ctx, uint64_t* captures, uint32_t* cached);

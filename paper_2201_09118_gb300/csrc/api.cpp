@@ -5,7 +5,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -1873,6 +1875,78 @@ int hd_phase_times(hd_ctx* c, double* ms, uint64_t* decodes) {
 }
 
 uint64_t hd_launch_count(hd_ctx* c) { return c ? c->launches : 0; }
+
+// GPU name without spaces (the key of a saved autotuner entry).
+static std::string gpu_key(int device) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  std::string k = prop.name;
+  for (char& ch : k)
+    if (ch == ' ' || ch == '\t' || ch == '\n') ch = '_';
+  return k;
+}
+
+int hd_autotune_save(hd_ctx* c, const char* path) {
+  if (!c || !path) return HD_ERR_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  const std::string gpu = gpu_key(c->device);
+  FILE* f = std::fopen(path, "w");
+  if (!f) return HD_ERR_ARG;
+  std::fprintf(f, "hd-autotune 1\n");
+  for (const auto& kv : c->tuned) {
+    const hd_config& x = kv.second;
+    std::fprintf(f, "%s %u %u %u %u %u %u %u %u %u %u\n", gpu.c_str(),
+                 std::get<0>(kv.first) ? 1u : 0u, std::get<1>(kv.first), std::get<2>(kv.first),
+                 std::get<3>(kv.first), x.subseq_bits, x.threads, x.window, x.lut_bits,
+                 x.cr_classes, x.decoder);
+  }
+  const bool ok = std::fclose(f) == 0;
+  return ok ? HD_OK : HD_ERR_ARG;
+}
+
+int hd_autotune_load(hd_ctx* c, const char* path, uint32_t* loaded) {
+  if (!c || !path || !loaded) return HD_ERR_ARG;
+  *loaded = 0;
+  std::lock_guard<std::mutex> lk(c->mu);
+  const std::string gpu = gpu_key(c->device);
+  FILE* f = std::fopen(path, "r");
+  if (!f) return HD_ERR_ARG;
+  char head[32] = {0};
+  int rc = HD_OK;
+  if (std::fscanf(f, "%31s", head) != 1 || std::strcmp(head, "hd-autotune") != 0) rc = HD_ERR_ARG;
+  unsigned ver = 0;
+  if (rc == HD_OK && (std::fscanf(f, "%u", &ver) != 1 || ver != 1)) rc = HD_ERR_ARG;
+  std::map<TuneKey, hd_config> got;
+  while (rc == HD_OK) {
+    char name[256];
+    unsigned ss, qb, lg, ms, S, B, W, K, cr, dec;
+    const int k = std::fscanf(f, "%255s %u %u %u %u %u %u %u %u %u %u", name, &ss, &qb, &lg, &ms,
+                              &S, &B, &W, &K, &cr, &dec);
+    if (k == EOF) break;
+    if (k != 11) {
+      rc = HD_ERR_ARG;
+      break;
+    }
+    // the same checks as hd_set_config: a shape the library would refuse is
+    // no entry
+    const hd_config x{S, B, W, K, cr, dec};
+    const bool okS = (S == 64 || S == 128 || S == 256 || S == 512);
+    const bool okB = B == 128 || B == 256 || B == 512 || ((B == 768 || B == 1024) && dec == 2);
+    if (!okS || !okB || (K && (K < 8 || K > 15)) || dec > 2 || cr > 32 || ss > 1) {
+      rc = HD_ERR_ARG;
+      break;
+    }
+    if (gpu == name) got[TuneKey{ss != 0, qb, lg, ms}] = x;
+  }
+  std::fclose(f);
+  if (rc) return rc;
+  for (const auto& kv : got) c->tuned[kv.first] = kv.second;
+  *loaded = static_cast<uint32_t>(got.size());
+  return HD_OK;
+}
 
 int hd_graph_stats(hd_ctx* c, uint64_t* captures, uint32_t* cached) {
   if (!c || !captures || !cached) return HD_ERR_ARG;

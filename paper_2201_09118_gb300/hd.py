@@ -135,6 +135,8 @@ _SIGS = {
     "hd_phase_times": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
                        ctypes.c_int),
     "hd_set_wait_limit": ([_P, ctypes.c_uint64], ctypes.c_int),
+    "hd_autotune_save": ([_P, ctypes.c_char_p], ctypes.c_int),
+    "hd_autotune_load": ([_P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "hd_kernel_time": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
                        ctypes.c_int),
     "hd_launch_count": ([_P], ctypes.c_uint64),
@@ -363,6 +365,17 @@ class Context:
                                                     _stream_handle(stream), ctypes.byref(cfg)))
         return {"subseq_bits": cfg.subseq_bits, "threads": cfg.threads, "window": cfg.window,
                 "lut_bits": cfg.lut_bits, "cr_classes": cfg.cr_classes, "decoder": cfg.decoder}
+
+    def autotune_save(self, path: str) -> None:
+        """Writes this context's tuned launch shapes to `path` (hd_autotune_save)."""
+        _check("hd_autotune_save", self._lib.hd_autotune_save(self.handle, path.encode()))
+
+    def autotune_load(self, path: str) -> int:
+        """Takes the tuned shapes of this GPU from `path`; returns how many."""
+        n = ctypes.c_uint32()
+        _check("hd_autotune_load", self._lib.hd_autotune_load(self.handle, path.encode(),
+                                                              ctypes.byref(n)))
+        return n.value
 
     def graph_stats(self):
         cap = ctypes.c_uint64()

@@ -179,3 +179,40 @@ def test_autotune_self_sync(ctx):
     ctx.decode_batch(fields, outs)
     assert ctx.batch_status(len(fields))[0] == 0
     check_outputs(comps, outs)
+
+
+def test_autotune_cache_saved_and_loaded_by_a_new_context(ctx, tmp_path):
+    from paper_2201_09118_gb300 import hd
+    comps, fields, outs = make_batch(8, 1 << 12, 1 << 17, 818)
+    best = ctx.autotune(fields, outs)
+    path = str(tmp_path / "tune.txt")
+    ctx.autotune_save(path)
+    lines = open(path).read().split("\n")
+    assert lines[0] == "hd-autotune 1" and len([ln for ln in lines[1:] if ln]) >= 1
+    c2 = hd.Context(0)
+    try:
+        assert c2.autotune_load(path) >= 1
+        reset(outs)
+        c2.decode_batch(fields, outs)
+        assert c2.batch_status(len(fields))[0] == 0
+        check_outputs(comps, outs)
+        got = c2.get_config()
+        for k in ("subseq_bits", "threads", "lut_bits"):
+            assert got[k] == best[k], (k, got, best)
+        # entries of another device are skipped, a file of another kind is refused
+        other = str(tmp_path / "other.txt")
+        with open(other, "w") as fh:
+            fh.write("hd-autotune 1\n")
+            for ln in lines[1:]:
+                if ln:
+                    fh.write("Some_Other_GPU " + ln.split(" ", 1)[1] + "\n")
+        assert c2.autotune_load(other) == 0
+        bad = str(tmp_path / "bad.txt")
+        with open(bad, "w") as fh:
+            fh.write("hd-autotune 1\nname 0 1 2\n")
+        with pytest.raises(hd.HDError):
+            c2.autotune_load(bad)
+        with pytest.raises(hd.HDError):
+            c2.autotune_load(str(tmp_path / "missing.txt"))
+    finally:
+        c2.close()
