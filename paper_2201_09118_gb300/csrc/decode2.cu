@@ -341,6 +341,9 @@ __global__ void __launch_bounds__(B, write_min_blocks<B>())
     if (t == 0 && tl + 1 == F.nunits && base + C != F.n) atomicOr(F.err, kErrCount);
     const bool zr = P.zero_runs && s_lmin == 1;
     const uint32_t sym0 = s_sym0;
+    // codes out: the window is pre-filled with the 1-bit code's symbol, so
+    // its runs need no stores (values: every position is written)
+    const bool prefilled = zr && !VALUES;
     auto decode = [&](uint16_t* dst) {
                       uint32_t p = gp;
                       bool bad = false;
@@ -353,7 +356,7 @@ __global__ void __launch_bounds__(B, write_min_blocks<B>())
                           if (!(w >> 31)) {
                             uint32_t z = w ? __clz(w) : 32u;
                             z = min(z, c - j);
-                            fill_u16(dst + j, z, sym0);
+                            if (!prefilled) fill_u16(dst + j, z, sym0);
                             j += z;
                             p += z;
                           } else {
@@ -382,7 +385,8 @@ __global__ void __launch_bounds__(B, write_min_blocks<B>())
                              static_cast<int32_t>(static_cast<uint32_t>(s_vtile[0])),
                              s_vtile[1], s_vtile[2], s_vw, decode);
     else
-      window_write<B>(s_out, &s_flush_end, P.window, o, c, C, base, F.out, F.n, decode);
+      window_write<B>(s_out, &s_flush_end, P.window, o, c, C, base, F.out, F.n, decode,
+                      prefilled, (sym0 & 0xFFFFu) * 0x10001u);
   }
 }
 

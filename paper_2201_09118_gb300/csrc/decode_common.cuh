@@ -276,18 +276,33 @@ __device__ __forceinline__ uint64_t lookback_counts(const DecodeParams& P, uint6
 // pass with two barriers does it.
 // `decode(dst)` writes the thread's c symbols to dst[0 .. c).
 // Requires window >= max c (c <= S).  Global writes are clipped to [0, n).
+// With `prefill` every window pass is first filled with the symbol pair
+// `fill2` by all threads (16-byte stores, one barrier), so that `decode`
+// may leave the positions of that symbol unwritten: runs of a field's
+// 1-bit code then cost no shared stores.  (Written by their own threads,
+// such runs put every thread of a warp on one bank when the subsequences
+// hold equal counts, as they do when almost every code is that 1-bit code.)
 template <int B, class DecodeFn>
 __device__ __forceinline__ void window_write(uint16_t* s_out, uint32_t* s_flush_end,
                                              uint32_t window, uint32_t o, uint32_t c,
                                              uint32_t C, uint64_t base, uint16_t* out,
-                                             uint64_t n, DecodeFn&& decode) {
+                                             uint64_t n, DecodeFn&& decode,
+                                             bool prefill = false, uint32_t fill2 = 0) {
   const int t = threadIdx.x;
   const uint32_t off0 = static_cast<uint32_t>((reinterpret_cast<uintptr_t>(out) >> 1) & 7u);
   // out - off0 is 16-byte aligned; virtual index X = x + off0
   uint16_t* out_al = out - off0;
+  // fills window symbols [0, 8 * ceil(m / 8)) with fill2 (s_out is 16-byte
+  // aligned and holds window + 16 symbols)
+  auto fill_window = [&](uint32_t m) {
+    const uint4 v = make_uint4(fill2, fill2, fill2, fill2);
+    for (uint32_t k = t; k < (m + 7) >> 3; k += B) reinterpret_cast<uint4*>(s_out)[k] = v;
+    __syncthreads();
+  };
   if (C <= window) {
     const uint64_t X0 = base + off0;
     const uint32_t pad = static_cast<uint32_t>(X0 & 7u);
+    if (prefill) fill_window(pad + C);
     if (c) decode(s_out + pad + o);
     __syncthreads();
     const uint64_t a0 = X0 - pad;
@@ -321,6 +336,7 @@ __device__ __forceinline__ void window_write(uint16_t* s_out, uint32_t* s_flush_
     const uint32_t fe = *s_flush_end;
     const uint64_t X0 = base + ws + off0;
     const uint32_t pad = static_cast<uint32_t>(X0 & 7u);
+    if (prefill) fill_window(pad + (fe - ws));
     if (!done && o + c <= fe) {
       decode(s_out + pad + (o - ws));
       done = true;

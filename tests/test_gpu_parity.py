@@ -370,6 +370,40 @@ def test_unaligned_output(ctx, shift, decoder):
     assert np.all(r[shift + c["n"]:] == np.uint16(CANARY))
 
 
+@pytest.mark.parametrize("case", ["skew1e-2", "one_symbol", "mixed"])
+@pytest.mark.parametrize("with_gap", [True, False], ids=["gap", "selfsync"])
+@pytest.mark.parametrize("S,threads,window", [(128, 128, 0), (128, 512, 256), (256, 256, 1024),
+                                              (128, 256, 4096)])
+def test_pre_filled_windows_of_1bit_runs(ctx, case, with_gap, S, threads, window):
+    # fields under 1.25 bits per code: the two-phase write kernel fills each
+    # window pass with the 1-bit code's symbol and stores only the other
+    # codes; small windows make tiles take several passes, and the output
+    # starts at an odd symbol so the window's pad is nonzero
+    rng = np.random.default_rng(S + threads + window)
+    if case == "skew1e-2":
+        x = synth.smooth_codes_1d(500001, 1e-2, seed=31)
+    elif case == "one_symbol":
+        x = np.full(262147, 512, np.uint16)
+    else:  # long runs of the 1-bit code broken by bursts of other codes
+        x = np.full(400003, 512, np.uint16)
+        for k in rng.integers(0, x.size - 300, 60):
+            x[k:k + rng.integers(1, 300)] = rng.integers(0, 1024, 1)[0]
+    c = oracle.compress(x, 1024, S=128)
+    assert c["nbits"] / c["n"] < 1.25
+    f = dev_field(c, with_gap)
+    buf = torch.full((c["n"] + 40,), CANARY, dtype=torch.int32).to(torch.int16).cuda()
+    ctx.set_config(decoder=1 if with_gap else 0, subseq_bits=S, threads=threads, window=window)
+    try:
+        ctx.decode(f, buf[3:])
+        assert ctx.status() == 0
+    finally:
+        ctx.reset_config()
+    r = buf.cpu().numpy().view(np.uint16)
+    assert np.all(r[:3] == np.uint16(CANARY))
+    assert np.array_equal(r[3:3 + c["n"]], expect(c))
+    assert np.all(r[3 + c["n"]:] == np.uint16(CANARY))
+
+
 # ---------------------------------------------------------------------------
 # full-size workload: the 512^3 field of Lorenzo codes
 # ---------------------------------------------------------------------------
