@@ -109,6 +109,15 @@ DECODER_KERNELS = {1: ("decode_gap", "k_count + k_scan + k_write"),
                    2: ("decode_gap_one_pass", "k_decode_warp")}
 
 
+def roofline_of(nbytes: float, ms: float, peak: float, peak_kind: str) -> dict:
+    """HBM roofline of a decode: algorithmic bytes over its time, against the
+    measured copy bandwidth."""
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind, "algorithmic_bytes": nbytes,
+            "kernel_ms": ms}
+
+
 def kernel_source_hash(kernel: str = "decode_gap") -> str:
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2201_09118_gb300", "csrc")
@@ -508,6 +517,7 @@ def run_skew(hd, torch, ctx_dev, stream, flush, n: int = 1 << 26, steps: int = 5
     import synth
     dev = f"cuda:{ctx_dev}"
     out = torch.empty(n, dtype=torch.int16, device=dev)
+    peak, _ = measured_peak()
     res = []
     for rel_eb, alphabet in ((1e-2, 256), (1e-4, 1024), (1e-6, 4096)):
         f1 = synth.fourier_field((n,), noise=1e-4, kmax=8, seed=1002)
@@ -538,6 +548,9 @@ def run_skew(hd, torch, ctx_dev, stream, flush, n: int = 1 << 26, steps: int = 5
             t = statistics.median(ms)
             row[name + "_ms"] = t
             row[name + "_gbps"] = 2.0 * n / (t * 1e-3) / 1e9
+            # algorithmic bytes: stream in (+ one gap byte per 128 bits), codes out
+            nb = (enc["nbits"] + 7) // 8 + 2 * n + (enc["nsub"] if name == "gap" else 0)
+            row[name + "_hbm_frac"] = nb / (t * 1e-3) / 1e9 / peak
             row[name + "_ok"] = bool(ok and ctx.status(stream) == 0)
         ctx.close()
         res.append(row)
@@ -898,7 +911,10 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "selfsync": {"value": whole_job_gbps(n, max(3, args.steps // 2), world, ms_ss),
                      "unit": "GB/s", "kernel_ms": kms_ss / max(1, kl_ss), "status": st_ss,
-                     "launch": launch_ss},
+                     "launch": launch_ss,
+                     # algorithmic bytes without a gap array: stream in, codes out
+                     "roofline": roofline_of((enc["nbits"] + 7) // 8 + 2 * n,
+                                             kms_ss / max(1, kl_ss), peak, peak_kind)},
     }
     line["encode"] = encode_leg
     line.update(extra)

@@ -388,6 +388,7 @@ __global__ void __launch_bounds__(B, write_min_blocks<B>())
       window_write<B>(s_out, &s_flush_end, P.window, o, c, C, base, F.out, F.n, decode,
                       prefilled, (sym0 & 0xFFFFu) * 0x10001u);
   }
+  if (!VALUES && t == 16) bulk_wait_all();  // the window copies are done
 }
 
 // Shared-memory window classes (the per-sequence compression-ratio classes of

@@ -28,6 +28,33 @@ __device__ __forceinline__ uint32_t ld_relaxed32(const uint32_t* p) {
   return v;
 }
 
+// Bulk stores of a staged output window by the TMA engine (cp.async.bulk,
+// shared to global).  The shared-memory writes that filled the window must be
+// made visible to that engine first: every writing thread runs
+// fence_async_smem() before the barrier after which one thread issues the
+// copy.  The issuing thread's groups are waited for with bulk_wait_read()
+// before the window is written again, and with bulk_wait_all() before the
+// thread exits.
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Copies `bytes` from shared address `src` to global `dst` as one bulk group.
+// Both addresses and the size must be multiples of 16; a request that is not
+// is refused (returns false, nothing issued) and the caller stores plainly.
+__device__ __forceinline__ bool bulk_store(void* dst, uint32_t src, uint32_t bytes) {
+  if (((reinterpret_cast<uintptr_t>(dst) | src | bytes) & 15u) != 0 || bytes == 0) return false;
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+               ::"l"(dst), "r"(src), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  return true;
+}
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ uint4 ldg_v4(const uint32_t* p) {
   return __ldg(reinterpret_cast<const uint4*>(p));
 }
@@ -267,6 +294,38 @@ __device__ __forceinline__ uint64_t lookback_counts(const DecodeParams& P, uint6
 }
 
 
+// Writes window symbols [lo, end) of a block's window (16-byte aligned,
+// shared) to dst[lo .. end) (dst 16-byte aligned): the 16-byte aligned middle
+// as one bulk copy by the TMA engine, issued by thread 16 and read before it
+// returns, the at most 7 symbols on either side by threads 0-15.  The threads
+// that wrote the window ran fence_async_smem() before the barrier preceding
+// this; the caller's next barrier follows the read.
+template <int B>
+__device__ __forceinline__ void flush_block(const uint16_t* s_out, uint16_t* dst, uint32_t lo,
+                                            uint32_t end) {
+  static_assert(B >= 32, "threads 0-16 take part");
+  const int t = threadIdx.x;
+  const uint32_t ra = (lo + 7) & ~7u, rb = end & ~7u;
+  if (rb > ra) {
+    if (t < 8) {
+      const uint32_t r = lo + t;
+      if (r < ra) dst[r] = s_out[r];
+    } else if (t < 16) {
+      const uint32_t r = rb + (t - 8);
+      if (r < end) dst[r] = s_out[r];
+    } else if (t == 16) {
+      const uint32_t src = static_cast<uint32_t>(__cvta_generic_to_shared(s_out + ra));
+      if (bulk_store(dst + ra, src, 2 * (rb - ra))) {
+        bulk_wait_read();
+      } else {
+        for (uint32_t r = ra; r < rb; ++r) dst[r] = s_out[r];
+      }
+    }
+  } else {
+    for (uint32_t r = lo + t; r < end; r += B) dst[r] = s_out[r];
+  }
+}
+
 // Algorithm 1 (Sec. IV-B): the block's output [0, C) is produced through a
 // shared-memory window of `window` symbols.  A thread decodes its whole range
 // [o, o + c) into the window only when it fits; the first thread that does
@@ -304,6 +363,7 @@ __device__ __forceinline__ void window_write(uint16_t* s_out, uint32_t* s_flush_
     const uint32_t pad = static_cast<uint32_t>(X0 & 7u);
     if (prefill) fill_window(pad + C);
     if (c) decode(s_out + pad + o);
+    fence_async_smem();
     __syncthreads();
     const uint64_t a0 = X0 - pad;
     uint16_t* dst = out_al + a0;
@@ -311,17 +371,7 @@ __device__ __forceinline__ void window_write(uint16_t* s_out, uint32_t* s_flush_
     const uint64_t Xn = n + off0;  // first virtual index past the output
     const uint32_t end_ok =
         a0 >= Xn ? 0u : (Xn - a0 < end_r ? static_cast<uint32_t>(Xn - a0) : end_r);
-    const uint32_t nvec = (end_r + 7) >> 3;
-    for (uint32_t v = t; v < nvec; v += B) {
-      const uint32_t r0 = v << 3;
-      if (r0 >= pad && r0 + 8 <= end_ok) {
-        *reinterpret_cast<uint4*>(dst + r0) = *reinterpret_cast<const uint4*>(s_out + r0);
-      } else {
-        const uint32_t lo = r0 > pad ? r0 : pad;
-        const uint32_t hi = r0 + 8 < end_ok ? r0 + 8 : end_ok;
-        for (uint32_t r = lo; r < hi; ++r) dst[r] = s_out[r];
-      }
-    }
+    if (end_ok > pad) flush_block<B>(s_out, dst, pad, end_ok);
     __syncthreads();
     return;
   }
@@ -341,24 +391,14 @@ __device__ __forceinline__ void window_write(uint16_t* s_out, uint32_t* s_flush_
       decode(s_out + pad + (o - ws));
       done = true;
     }
+    fence_async_smem();
     __syncthreads();
-    // store virtual range [X0, Xe) from s_out[X - a0]
+    // store virtual range [X0, Xe), clipped to Xn, from s_out[X - a0]
     const uint64_t a0 = X0 & ~7ull;
     const uint64_t Xe = base + fe + off0;
     const uint64_t Xn = n + off0;  // first virtual index past the output
-    const uint64_t q0 = a0 >> 3, q1 = (Xe + 7) >> 3;
-    for (uint64_t q = q0 + t; q < q1; q += B) {
-      const uint64_t Xq = q << 3;
-      if (Xq >= X0 && Xq + 8 <= Xe && Xq + 8 <= Xn) {
-        *reinterpret_cast<uint4*>(out_al + Xq) =
-            *reinterpret_cast<const uint4*>(s_out + (Xq - a0));
-      } else {
-        const uint64_t lo = Xq > X0 ? Xq : X0;
-        uint64_t hi = Xq + 8 < Xe ? Xq + 8 : Xe;
-        hi = hi < Xn ? hi : Xn;
-        for (uint64_t X = lo; X < hi; ++X) out_al[X] = s_out[X - a0];
-      }
-    }
+    const uint64_t Xend = Xe < Xn ? Xe : Xn;
+    if (Xend > X0) flush_block<B>(s_out, out_al + a0, pad, static_cast<uint32_t>(Xend - a0));
     __syncthreads();
     ws = fe;
   }

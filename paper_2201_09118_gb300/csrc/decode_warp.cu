@@ -241,22 +241,29 @@ __device__ __forceinline__ uint32_t walk_fixed(const uint32_t (&r)[S / 32 + 1], 
 
 // Writes window indices [lo, hi) (16-byte aligned window; index r is virtual
 // output index a0 + r, a0 a multiple of 8) to out_al, clipped to virtual
-// indices below Xn.
+// indices below Xn.  The 16-byte aligned middle goes out as one bulk copy by
+// the TMA engine, issued by lane 0 (the lanes ran fence_async_smem() after
+// writing the window; lane 0 waits for the copy's read before the window is
+// written again); the at most 7 symbols before and after it, plain.
 __device__ __forceinline__ void flush_window(uint32_t win_a, const uint16_t* win, uint32_t lo,
                                              uint32_t hi, uint64_t a0, uint16_t* out_al,
                                              uint64_t Xn, int lane) {
-  const uint32_t nq = (hi + 7) >> 3;
-  for (uint32_t q = (lo >> 3) + lane; q < nq; q += 32) {
-    const uint32_t r0 = q << 3;
-    const uint64_t Xq = a0 + r0;
-    if (r0 >= lo && r0 + 8 <= hi && Xq + 8 <= Xn) {
-      *reinterpret_cast<uint4*>(out_al + Xq) = lds_v4(win_a + 2 * r0);
-    } else {
-      const uint32_t b = r0 > lo ? r0 : lo;
-      const uint32_t e = r0 + 8 < hi ? r0 + 8 : hi;
-      for (uint32_t x = b; x < e; ++x)
-        if (a0 + x < Xn) out_al[a0 + x] = win[x];
+  const uint32_t end =
+      a0 + hi <= Xn ? hi : (Xn > a0 + lo ? static_cast<uint32_t>(Xn - a0) : lo);
+  const uint32_t ra = (lo + 7) & ~7u, rb = end & ~7u;
+  if (rb > ra) {
+    if (lane < 8) {
+      const uint32_t r = lo + lane;
+      if (r < ra) out_al[a0 + r] = win[r];
+    } else if (lane < 16) {
+      const uint32_t r = rb + (lane - 8);
+      if (r < end) out_al[a0 + r] = win[r];
+    } else if (lane == 16) {
+      if (!bulk_store(out_al + a0 + ra, win_a + 2 * ra, 2 * (rb - ra)))
+        for (uint32_t r = ra; r < rb; ++r) out_al[a0 + r] = win[r];
     }
+  } else {
+    for (uint32_t r = lo + lane; r < end; r += 32) out_al[a0 + r] = win[r];
   }
 }
 
@@ -385,6 +392,9 @@ __device__ __forceinline__ void write_tile(const WarpCtx& W, const TileRes& R, u
   constexpr uint32_t kMask16 = sizeof(E) == 2 ? 0x0FFFu : 0xFFFFu;
   constexpr uint32_t kMask32 = kMask16 | (kMask16 << 16);
   const uint32_t c = R.c, o = R.o, C = R.C;
+  // the previous tile's bulk copy must have read the window
+  if (lane == 16) bulk_wait_read();
+  __syncwarp();
   if (!R.overflow) {
     const uint64_t X0 = base + W.off0;
     const uint32_t pad = static_cast<uint32_t>(X0 & 7u);
@@ -408,6 +418,7 @@ __device__ __forceinline__ void write_tile(const WarpCtx& W, const TileRes& R, u
       }
       if ((c - par) & 1u) sts_u16(W.win_a + 2 * (x0 + c - 1), lds_u16(src) & kMask16);
     }
+    fence_async_smem();
     __syncwarp();
     flush_window(W.win_a, W.win, pad, pad + C, X0 - pad, W.out_al, W.Xn, lane);
     __syncwarp();
@@ -443,8 +454,10 @@ __device__ __forceinline__ void write_tile(const WarpCtx& W, const TileRes& R, u
         walk<S, E, true>(in.bits.u, R.start, end, W.lut_a, W.shift, W.T, W.lmin, bad2, put);
       }
     }
+    fence_async_smem();
     __syncwarp();
     flush_window(W.win_a, W.win, pad, pad + (we - ws), X0 - pad, W.out_al, W.Xn, lane);
+    if (lane == 16) bulk_wait_read();
     __syncwarp();
   }
 }
@@ -640,6 +653,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1)
     }
     rw = rn;
   }
+  if (lane == 16) bulk_wait_all();  // the last window copies are done
 }
 
 template <int S, int NW>
