@@ -179,6 +179,27 @@ int hd_status(hd_ctx* ctx, void* stream);
  * via hd_status. */
 int hd_sync_points(hd_ctx* ctx, const hd_field* f, uint8_t* gap_out, void* stream);
 
+/* Inspection of the per-prefix decode tables the kernels build from a code-
+ * length table (Sec. II-B canonical codes; the first-level tables of a1), for
+ * tests and tools.  Builds the tables of `lengths` (a DEVICE pointer,
+ * `alphabet` entries, 2 .. 4096) with K first-level bits (8 .. 15) in a
+ * temporary device buffer of its own, exactly as a decode on this context
+ * builds them, and copies the 2^K entries of each requested table to the host
+ * (any pointer may be NULL):
+ *   lut16[p]: for a code of at most K bits at prefix p, its length << 12 |
+ *             its symbol; else 0 << 12 | the smallest length under p, with
+ *             bit 11 (0x800) set when p holds codes of several lengths;
+ *   len8[p]:  the code length when every code under p has one length, else
+ *             0x80 | the smallest length (33: no code);
+ *   run8[p]:  m << 4 | b: the m (1 .. 7) codes that lie wholly within the K
+ *             bits of p, decoded one after another from the first, take b
+ *             bits; 0 when the first code is longer than K bits.
+ * Synchronous on `stream`.  HD_ERR_ARG for bad arguments, HD_ERR_CORRUPT for a
+ * length table that is no prefix code, HD_ERR_CUDA when an allocation or copy
+ * fails. */
+int hd_inspect_tables(hd_ctx* ctx, const uint8_t* lengths, uint32_t alphabet, uint32_t K,
+                      uint16_t* lut16, uint8_t* len8, uint8_t* run8, void* stream);
+
 /* Decodes nf independent fields of any sizes (device pointers, own codebooks;
  * Sec. III-C / III-B per field) with one CUDA graph launch for all gap-array
  * fields and one for all self-synchronising fields; d_outs[i] receives field

@@ -1226,6 +1226,53 @@ int hd_sync_points(hd_ctx* c, const hd_field* f, uint8_t* gap_out, void* stream)
   return decode_impl(c, f, nullptr, gap_out, stream);
 }
 
+int hd_inspect_tables(hd_ctx* c, const uint8_t* lengths, uint32_t alphabet, uint32_t K,
+                      uint16_t* lut16, uint8_t* len8, uint8_t* run8, void* stream) {
+  if (!c || !lengths || alphabet < 2 || alphabet > 4096 || K < 8 || K > 15) return HD_ERR_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // error word | table, in a buffer of its own (the context's workspace may
+  // still be in use by queued decodes)
+  const size_t tab_off = 256;
+  const size_t bytes = tab_off + hd::table_bytes(K, alphabet);
+  char* buf = nullptr;
+  if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return HD_ERR_CUDA;
+  }
+  FieldDesc d{};
+  d.lengths = lengths;
+  d.alphabet = alphabet;
+  d.table = reinterpret_cast<const hd::TableHeader*>(buf + tab_off);
+  d.err = reinterpret_cast<uint32_t*>(buf);
+  hd::PrepParams pp{};
+  pp.f0 = d;
+  pp.nfields = 1;
+  pp.slices = kTableSlices;
+  pp.table_blocks = kTableSlices;
+  pp.K = K;
+  int rc = HD_OK;
+  uint32_t status = 1;
+  const size_t n = size_t{1} << K;
+  if (cudaMemsetAsync(buf, 0, tab_off, st) != cudaSuccess ||
+      hd::launch_prepare(pp, st) != cudaSuccess ||
+      cudaMemcpyAsync(&status, buf + tab_off, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      (lut16 && cudaMemcpyAsync(lut16, buf + tab_off + hd::table_lut16_off(K, alphabet), 2 * n,
+                                cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+      (len8 && cudaMemcpyAsync(len8, buf + tab_off + hd::table_len8_off(K, alphabet), n,
+                               cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+      (run8 && cudaMemcpyAsync(run8, buf + tab_off + hd::table_run8_off(K, alphabet), n,
+                               cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    rc = HD_ERR_CUDA;
+  }
+  cudaFree(buf);
+  if (rc == HD_OK && status != 0) rc = HD_ERR_CORRUPT;
+  return rc;
+}
+
 int hd_status(hd_ctx* c, void* stream) {
   if (!c) return HD_ERR_ARG;
   std::lock_guard<std::mutex> lk(c->mu);
