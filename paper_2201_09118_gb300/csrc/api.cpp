@@ -507,8 +507,11 @@ int queue_decode_one_pass(hd_ctx* c, std::vector<FieldDesc>& descs, const hd::La
   hd::LaunchShape s = shape;
   const double bits_per =
       static_cast<double>(d.nbits) / static_cast<double>(d.n ? d.n : 1);
-  s.long_cap = static_cast<uint32_t>(align_up(std::min<uint32_t>(d.alphabet, 4096), 8));
   if (s.K == 0) s.K = hd::lut16_usable(kDefaultK16, d.alphabet) ? kDefaultK16 : kDefaultK;
+  // long-code symbols in shared memory (codes past the second-level tables);
+  // none with 14+ table bits, whose first-level table takes that room
+  s.long_cap = s.K >= 14 ? 0u
+                         : static_cast<uint32_t>(align_up(std::min<uint32_t>(d.alphabet, 4096), 8));
   s.lut16 = hd::lut16_usable(s.K, d.alphabet) ? 1u : 0u;
   s.runs = 0;
   s.decoder = 2;

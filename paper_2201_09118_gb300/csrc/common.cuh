@@ -82,6 +82,14 @@ __host__ __device__ constexpr uint64_t table_run8_off(uint32_t K, uint32_t A) {
 // L <= K + sub_bits whose first K + sub_bits bits are prefix sub_p0 + s then q,
 // else 0 (a longer code, or no code: the limits are walked).
 constexpr uint32_t kSubCap = 4096;
+// Second-level entries in use for K first-level bits: all kSubCap below 14
+// bits; half of them from 14 bits on, where fewer codes are longer than the
+// first level and the one-pass decoder's shared memory holds a first-level
+// table twice as large (the prefixes past the capacity keep the walk of the
+// canonical limits).
+__host__ __device__ constexpr uint32_t sub_cap(uint32_t K) {
+  return K >= 14 ? kSubCap / 2 : kSubCap;
+}
 __host__ __device__ constexpr uint64_t table_sub_off(uint32_t K, uint32_t A) {
   return (table_run8_off(K, A) + (static_cast<uint64_t>(1) << K) + 15) &
          ~static_cast<uint64_t>(15);

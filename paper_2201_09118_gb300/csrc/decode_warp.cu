@@ -494,13 +494,13 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1)
   const uint32_t cmax = P.cmax;
   // shared memory: first-level table | second-level tables | per-warp
   // columns and windows | long-code symbols
-  const uint32_t lut_b = lut_bytes(kKind, P.K) + 2 * kSubCap;
+  const uint32_t lut_b = lut_bytes(kKind, P.K) + 2 * sub_cap(P.K);
   unsigned char* s_lut = smem;
   uint16_t* s_sub = reinterpret_cast<uint16_t*>(smem + lut_bytes(kKind, P.K));
   uint16_t* s_long = reinterpret_cast<uint16_t*>(smem + lut_b + NW * warp_bytes(cmax));
   load_table(F.table, P.K, F.alphabet, kKind, s_lut, s_end, s_base, s_meta, (NW + 1) * 32, s_long,
              P.long_cap);
-  const uint32_t sub_n = F.table->nsub << F.table->sub_bits;  // entries in use (<= kSubCap)
+  const uint32_t sub_n = F.table->nsub << F.table->sub_bits;  // entries in use (<= sub_cap(K))
   {
     const uint4* src = reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(F.table) +
                                                       table_sub_off(P.K, F.alphabet));
@@ -701,7 +701,8 @@ cudaError_t launch_s(const DecodeParams& p, const LaunchShape& s, int num_sms,
 
 size_t warp_decode_smem_bytes(const LaunchShape& s) {
   const size_t lut = dev::lut_bytes(s.lut16 ? dev::Lut::k16 : dev::Lut::k32, s.K);
-  size_t b = lut + 2 * kSubCap + static_cast<size_t>(s.threads / 32 - 1) * warp_bytes(s.cmax);
+  size_t b = lut + 2 * sub_cap(s.K);
+  b += static_cast<size_t>(s.threads / 32 - 1) * warp_bytes(s.cmax);
   b += static_cast<size_t>(s.long_cap) * 2;
   return (b + 15) & ~static_cast<size_t>(15);
 }

@@ -180,7 +180,7 @@ __device__ void build_table(const FieldDesc& F, uint32_t K, uint32_t sl, uint32_
   // Second-level tables of the 16-bit table.  Canonical codes longer than K
   // bits are the windows from end[K] on, so their prefixes are consecutive:
   // [end[K] >> (32-K), ceil(end[maxlen] / 2^(32-K))).  Each gets sub_bits more
-  // bits (as many as the longest code needs, at most 8, and as the kSubCap
+  // bits (as many as the longest code needs, at most 8, and as the sub_cap(K)
   // entries allow); the most probable long codes come first.
   __shared__ uint32_t s_sub[3];  // sub_bits, nsub, sub_p0
   if (t == 0) {
@@ -191,7 +191,8 @@ __device__ void build_table(const FieldDesc& F, uint32_t K, uint32_t sl, uint32_
       const uint64_t p1 = (s_end[maxlen] + (1ull << sh) - 1) >> sh;
       kb = maxlen - K < 8 ? maxlen - K : 8;
       const uint64_t nlong = p1 > p0 ? p1 - p0 : 0;
-      ns = static_cast<uint32_t>(nlong < (kSubCap >> kb) ? nlong : (kSubCap >> kb));
+      const uint32_t cap = sub_cap(K) >> kb;
+      ns = static_cast<uint32_t>(nlong < cap ? nlong : cap);
     }
     s_sub[0] = kb;
     s_sub[1] = ns;
