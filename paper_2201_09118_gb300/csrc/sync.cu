@@ -51,10 +51,28 @@ struct CountT<256> {
 
 
 // Decodes codewords (lengths only) from p while p < end; returns the stop.
+// When the codebook has a 1-bit code (canonically the bit 0, every other code
+// starting with 1), z zero bits at a codeword boundary are z such codes, taken
+// with one leading-zero count: the same stop and count as one code at a time.
 template <int STRIDE>
 __device__ __forceinline__ uint32_t walk(const Tables& T, const uint32_t* col, uint32_t p,
                                          uint32_t end, uint32_t& c) {
   bool bad = false;
+  if (T.end[1] != 0) {
+    while (p < end) {
+      const uint32_t w = peek<STRIDE>(col, p);
+      if (!(w >> 31)) {
+        uint32_t z = w ? __clz(w) : 32u;
+        z = min(z, end - p);
+        p += z;
+        c += z;
+      } else {
+        p += code_len8(T, w, bad);
+        ++c;
+      }
+    }
+    return p;
+  }
   while (p < end) {
     p += code_len8(T, peek<STRIDE>(col, p), bad);
     ++c;
@@ -182,9 +200,15 @@ __global__ void __launch_bounds__(kGuessThreads) k_guess(const __grid_constant__
         const uint8_t* len8 =
             reinterpret_cast<const uint8_t*>(H) + table_len8_off(P.K, Fp->alphabet);
         const uint32_t shift = 32u - P.K, maxlen = H->maxlen;
+        const bool zr = H->end[1] != 0;  // a 1-bit code: runs of zero bits (see walk)
         uint32_t pos = 0;
         while (pos < first) {
           const uint32_t w = peek<kGuessThreads>(col, pos);
+          if (zr && !(w >> 31)) {
+            const uint32_t z = w ? __clz(w) : 32u;
+            pos += min(z, first - pos);
+            continue;
+          }
           uint32_t L = __ldg(len8 + (w >> shift));
           if (L & kLen8Walk) {
             L &= 0x7Fu;
