@@ -193,12 +193,18 @@ int hd_sync_points(hd_ctx* ctx, const hd_field* f, uint8_t* gap_out, void* strea
  *             0x80 | the smallest length (33: no code);
  *   run8[p]:  m << 4 | b: the m (1 .. 7) codes that lie wholly within the K
  *             bits of p, decoded one after another from the first, take b
- *             bits; 0 when the first code is longer than K bits.
+ *             bits; 0 when the first code is longer than K bits;
+ *   pair[p]:  the two-code entry of the decode-and-write kernel: m (the codes
+ *             of p's K bits it resolves, up to two) << 30; m = 2 (alphabets
+ *             up to 1024): first length << 26 | second length << 22 | second
+ *             symbol << 10 | first symbol; m = 1: first length << 26 | its
+ *             symbol; m = 0: as lut16 for a longer first code.
  * Synchronous on `stream`.  HD_ERR_ARG for bad arguments, HD_ERR_CORRUPT for a
  * length table that is no prefix code, HD_ERR_CUDA when an allocation or copy
  * fails. */
 int hd_inspect_tables(hd_ctx* ctx, const uint8_t* lengths, uint32_t alphabet, uint32_t K,
-                      uint16_t* lut16, uint8_t* len8, uint8_t* run8, void* stream);
+                      uint16_t* lut16, uint8_t* len8, uint8_t* run8, uint32_t* pair,
+                      void* stream);
 
 /* Decodes nf independent fields of any sizes (device pointers, own codebooks;
  * Sec. III-C / III-B per field) with one CUDA graph launch for all gap-array

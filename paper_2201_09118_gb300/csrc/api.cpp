@@ -309,8 +309,11 @@ int prepare_launch(const hd_ctx* c, std::vector<FieldDesc>& descs, const hd::Lau
   // 16-bit first-level entries when every field's symbols fit 12 bits
   s.lut16 = hd::lut16_usable(s.K, amax) ? 1u : 0u;
   // run table for counting when codes are short (measured: +24% decode at
-  // 1.9 bits per code, -6% at 9 bits)
-  s.runs = bits_per < kZeroRunsBelowBits ? 3u : bits_per < kRunsBelowBits ? 1u : 0u;
+  // 1.9 bits per code, -6% at 9 bits), and there two codes per lookup in the
+  // decode-and-write kernel (fields under 1.25 bits write runs instead)
+  s.runs = bits_per < kZeroRunsBelowBits ? 3u
+           : bits_per < kRunsBelowBits   ? (1u | hd::kShapePairs)
+                                         : 0u;
   if (s.window == 0) {
     // output window: about 1.2x a tile's expected symbol count, rounded up to
     // a multiple of 2048 so that batches of similar code lengths share a shape
@@ -1230,7 +1233,8 @@ int hd_sync_points(hd_ctx* c, const hd_field* f, uint8_t* gap_out, void* stream)
 }
 
 int hd_inspect_tables(hd_ctx* c, const uint8_t* lengths, uint32_t alphabet, uint32_t K,
-                      uint16_t* lut16, uint8_t* len8, uint8_t* run8, void* stream) {
+                      uint16_t* lut16, uint8_t* len8, uint8_t* run8, uint32_t* pair,
+                      void* stream) {
   if (!c || !lengths || alphabet < 2 || alphabet > 4096 || K < 8 || K > 15) return HD_ERR_ARG;
   std::lock_guard<std::mutex> lk(c->mu);
   DeviceGuard g(c->device);
@@ -1266,6 +1270,8 @@ int hd_inspect_tables(hd_ctx* c, const uint8_t* lengths, uint32_t alphabet, uint
       (len8 && cudaMemcpyAsync(len8, buf + tab_off + hd::table_len8_off(K, alphabet), n,
                                cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
       (run8 && cudaMemcpyAsync(run8, buf + tab_off + hd::table_run8_off(K, alphabet), n,
+                               cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+      (pair && cudaMemcpyAsync(pair, buf + tab_off + hd::table_pair_off(K, alphabet), 4 * n,
                                cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();

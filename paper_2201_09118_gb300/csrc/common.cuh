@@ -94,6 +94,19 @@ __host__ __device__ constexpr uint64_t table_sub_off(uint32_t K, uint32_t A) {
   return (table_run8_off(K, A) + (static_cast<uint64_t>(1) << K) + 15) &
          ~static_cast<uint64_t>(15);
 }
+// Two-code first-level entry (uint32[2^K] after the second-level tables,
+// 16-byte aligned), read by the decode-and-write kernel of fields under four
+// bits per code: bits 30..31 hold m, the codes of at most K bits that lie
+// wholly within the prefix's K bits, counted from the first up to two.
+//   m = 2: first length (bits 26..29), second length (22..25), second symbol
+//          (10..19), first symbol (0..9) -- alphabets up to 1024 only;
+//   m = 1: first length (26..29) and symbol (0..11);
+//   m = 0: the first code is longer than K bits (or is no code): the low bits
+//          as in the 16-bit entry (smallest length, kLut16Mixed).
+__host__ __device__ constexpr uint64_t table_pair_off(uint32_t K, uint32_t A) {
+  return table_sub_off(K, A) + 2ull * kSubCap;
+}
+
 __host__ __device__ constexpr bool lut16_usable(uint32_t K, uint32_t A) {
   return A <= 4096 && K <= 15;
 }

@@ -21,6 +21,8 @@
 // entries and counts into registers while they decode the current tile.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -262,7 +264,8 @@ template <int S, int B, class E, bool VALUES>
 __global__ void __launch_bounds__(B, write_min_blocks<B>())
     k_write(const __grid_constant__ DecodeParams P) {
   constexpr int W = S / 32 + 1;
-  constexpr Lut kKind = sizeof(E) == 2 ? Lut::k16 : Lut::k32;
+  constexpr bool kPairs = std::is_same_v<E, PairEntry>;
+  constexpr Lut kKind = kPairs ? Lut::kPair : sizeof(E) == 2 ? Lut::k16 : Lut::k32;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* s_lut = smem;
   uint32_t* s_bits = reinterpret_cast<uint32_t*>(smem + lut_bytes(kKind, P.K));
@@ -366,12 +369,32 @@ __global__ void __launch_bounds__(B, write_min_blocks<B>())
                           }
                         }
                       }
-                      for (; j + 1 < c; j += 2) {
-                        uint32_t s0, s1;
-                        p += code_sym_t<E>(T, peek<B>(col, p), s0, bad);
-                        p += code_sym_t<E>(T, peek<B>(col, p), s1, bad);
-                        dst[j] = static_cast<uint16_t>(s0);
-                        dst[j + 1] = static_cast<uint16_t>(s1);
+                      if constexpr (kPairs) {
+                        // two codes per lookup when both lie within the
+                        // first-level bits (the entry's m = 2)
+                        const uint32_t* pt = static_cast<const uint32_t*>(T.lut);
+                        while (j + 1 < c) {
+                          const uint32_t w = peek<B>(col, p);
+                          const uint32_t e = pt[w >> T.shift];
+                          if ((e >> 30) == 2u) {
+                            dst[j] = static_cast<uint16_t>(e & 0x3FFu);
+                            dst[j + 1] = static_cast<uint16_t>((e >> 10) & 0x3FFu);
+                            p += ((e >> 26) & 15u) + ((e >> 22) & 15u);
+                            j += 2;
+                          } else {
+                            uint32_t s0;
+                            p += code_sym_pair(T, w, e, s0, bad);
+                            dst[j++] = static_cast<uint16_t>(s0);
+                          }
+                        }
+                      } else {
+                        for (; j + 1 < c; j += 2) {
+                          uint32_t s0, s1;
+                          p += code_sym_t<E>(T, peek<B>(col, p), s0, bad);
+                          p += code_sym_t<E>(T, peek<B>(col, p), s1, bad);
+                          dst[j] = static_cast<uint16_t>(s0);
+                          dst[j + 1] = static_cast<uint16_t>(s1);
+                        }
                       }
                       if (j < c) {
                         uint32_t s0;
@@ -435,6 +458,11 @@ cudaError_t launch_scan(const DecodeParams& p, cudaStream_t stream) {
 template <int S, int B, bool VALUES = false>
 cudaError_t launch_write_sb(const DecodeParams& p, const LaunchShape& s, int num_sms,
                             cudaStream_t stream) {
+  if constexpr (S <= 256) {
+    if (s.lut16 && (s.runs & kShapePairs))
+      return launch_persistent(k_write<S, B, PairEntry, VALUES>, p, B, two_phase_smem_bytes(s),
+                               num_sms, s.grid, stream);
+  }
   if (s.lut16)
     return launch_persistent(k_write<S, B, uint16_t, VALUES>, p, B, two_phase_smem_bytes(s),
                              num_sms, s.grid, stream);
@@ -522,7 +550,10 @@ cudaError_t launch_write_s(const DecodeParams& p, const LaunchShape& s, int num_
 
 size_t two_phase_smem_bytes(const LaunchShape& s) {
   const size_t W = s.S / 32 + 1;
-  size_t b = dev::lut_bytes(s.lut16 ? dev::Lut::k16 : dev::Lut::k32, s.K) + W * s.threads * 4;
+  const dev::Lut kind = s.lut16 && (s.runs & kShapePairs) && s.S <= 256 ? dev::Lut::kPair
+                        : s.lut16                                       ? dev::Lut::k16
+                                                                        : dev::Lut::k32;
+  size_t b = dev::lut_bytes(kind, s.K) + W * s.threads * 4;
   b += (static_cast<size_t>(s.window) + 16) * 2;
   b += static_cast<size_t>(s.long_cap) * 2;
   return (b + 15) & ~static_cast<size_t>(15);

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -166,11 +167,37 @@ __device__ __forceinline__ uint32_t code_sym16(const Tables& T, uint32_t w, uint
   return L;
 }
 
-// Entry type of the symbol table: E = uint32_t or uint16_t.
+// Entry type of the two-code table (see table_pair_off).
+struct PairEntry {};
+
+// Length and symbol of the first codeword at window w from the two-code
+// table (entry e = the table's entry for w).
+__device__ __forceinline__ uint32_t code_sym_pair(const Tables& T, uint32_t w, uint32_t e,
+                                                  uint32_t& sym, bool& bad) {
+  const uint32_t m = e >> 30;
+  if (m) {
+    sym = m == 1 ? (e & 0xFFFu) : (e & 0x3FFu);
+    return (e >> 26) & 15u;
+  }
+  uint32_t L = e & 0xFFu;
+  if (e & kLut16Mixed) {
+    L = walk_len(T, w, L, bad);
+    if (!L) {
+      sym = 0;
+      return 1;
+    }
+  }
+  sym = long_sym(T, w, L);
+  return L;
+}
+
+// Entry type of the symbol table: E = uint32_t, uint16_t or PairEntry.
 template <class E>
 __device__ __forceinline__ uint32_t code_sym_t(const Tables& T, uint32_t w, uint32_t& sym,
                                                bool& bad) {
-  if constexpr (sizeof(E) == 2) {
+  if constexpr (std::is_same_v<E, PairEntry>) {
+    return code_sym_pair(T, w, static_cast<const uint32_t*>(T.lut)[w >> T.shift], sym, bad);
+  } else if constexpr (sizeof(E) == 2) {
     return code_sym16(T, w, sym, bad);
   } else {
     return code_sym(T, w, sym, bad);
@@ -552,10 +579,10 @@ __device__ __forceinline__ void window_write_values(uint16_t* s_out, uint32_t* s
 
 // Which first-level table a kernel keeps in shared memory.
 // k8r: the length table followed by the run table (2 x 2^K bytes).
-enum class Lut { k32, k16, k8, k8r };
+enum class Lut { k32, k16, k8, k8r, kPair };
 
 __host__ __device__ constexpr uint32_t lut_bytes(Lut kind, uint32_t K) {
-  return kind == Lut::k32 ? (4u << K)
+  return kind == Lut::k32 || kind == Lut::kPair ? (4u << K)
          : kind == Lut::k16 ? (2u << K)
          : kind == Lut::k8r ? (2u << K)
                             : (1u << K);
@@ -571,9 +598,10 @@ __device__ __forceinline__ void load_table(const TableHeader* H, uint32_t K, uin
                                            uint16_t* s_long = nullptr, uint32_t long_cap = 0) {
   const int t = threadIdx.x;
   const char* tb = reinterpret_cast<const char*>(H);
-  const uint64_t off = kind == Lut::k32   ? kTableHeaderBytes
-                       : kind == Lut::k16 ? table_lut16_off(K, alphabet)
-                                          : table_len8_off(K, alphabet);
+  const uint64_t off = kind == Lut::k32     ? kTableHeaderBytes
+                       : kind == Lut::k16   ? table_lut16_off(K, alphabet)
+                       : kind == Lut::kPair ? table_pair_off(K, alphabet)
+                                            : table_len8_off(K, alphabet);
   const uint4* src = reinterpret_cast<const uint4*>(tb + off);
   uint4* dst = reinterpret_cast<uint4*>(s_lut);
   const uint32_t nv = lut_bytes(kind, K) / 16;

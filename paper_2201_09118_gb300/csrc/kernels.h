@@ -27,9 +27,13 @@ struct LaunchShape {
   uint32_t grid;     // persistent blocks (0: full occupancy)
   uint32_t lut16;    // 1: the decode-and-write kernel uses 16-bit first-level entries
   uint32_t runs;     // bit 0: the count kernel takes several short codes per lookup (run
-                     // table); bit 1: runs of a 1-bit code are counted and written whole
+                     // table); bit 1: runs of a 1-bit code are counted and written whole;
+                     // bit 2 (kShapePairs): the decode-and-write kernel of 16-bit tables
+                     // takes two codes per lookup (two-code table, S up to 256)
   uint32_t decoder;  // 0 automatic, 1 two phases, 2 one pass (hd_config.decoder)
 };
+
+constexpr uint32_t kShapePairs = 4u;
 
 // Dynamic shared memory of the single-pass gap-array kernel.
 size_t decode_smem_bytes(const LaunchShape& s);

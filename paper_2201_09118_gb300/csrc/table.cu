@@ -43,6 +43,7 @@ __device__ void build_table(const FieldDesc& F, uint32_t K, uint32_t sl, uint32_
   uint16_t* lut16 = reinterpret_cast<uint16_t*>(tb + table_lut16_off(K, A));
   uint8_t* len8 = reinterpret_cast<uint8_t*>(tb + table_len8_off(K, A));
   uint8_t* run8 = reinterpret_cast<uint8_t*>(tb + table_run8_off(K, A));
+  uint32_t* pair = reinterpret_cast<uint32_t*>(tb + table_pair_off(K, A));
   const bool with16 = lut16_usable(K, A);
 
   if (t < 34) {
@@ -141,12 +142,25 @@ __device__ void build_table(const FieldDesc& F, uint32_t K, uint32_t sl, uint32_
     const uint32_t w = p << (32 - K);
     uint32_t L = 1;
     while (L <= 32 && static_cast<uint64_t>(w) >= s_end[L]) ++L;
-    uint32_t e, e16, e8, r8 = 0;
+    uint32_t e, e16, e8, r8 = 0, pe;
     if (L <= K && L <= maxlen) {
       const uint32_t rank = (w >> (32 - L)) + s_base[L];
       e = (L << 16) | sorted[rank];
       e16 = (L << 12) | (sorted[rank] & 0xFFFu);
       e8 = L;
+      // the two-code entry: a second code wholly within the K bits joins
+      // the first when both symbols fit 10 bits
+      pe = (1u << 30) | (L << 26) | (sorted[rank] & 0xFFFu);
+      if (A <= 1024 && L < K) {
+        const uint32_t rem = K - L, w2 = w << L;
+        uint32_t L2 = 1;
+        while (L2 <= rem && static_cast<uint64_t>(w2) >= s_end[L2]) ++L2;
+        if (L2 <= rem && L2 <= maxlen) {
+          const uint32_t sym1 = sorted[(w2 >> (32 - L2)) + s_base[L2]];
+          pe = (2u << 30) | (L << 26) | (L2 << 22) | ((sym1 & 0x3FFu) << 10) |
+               (sorted[rank] & 0x3FFu);
+        }
+      }
       // further codes wholly within the K known bits: a code of length
       // L2 <= the bits left is fixed by them (the limits are left-aligned)
       uint32_t used = L, m = 1;
@@ -170,9 +184,13 @@ __device__ void build_table(const FieldDesc& F, uint32_t K, uint32_t sl, uint32_
       e = kLongFlag | (lmax << 8) | lmin;
       e16 = lmin | (lmin == lmax ? 0u : kLut16Mixed);
       e8 = lmin == lmax ? lmin : (kLen8Walk | lmin);
+      pe = e16;  // m = 0
     }
     lut[p] = e;
-    if (with16) lut16[p] = static_cast<uint16_t>(e16);
+    if (with16) {
+      lut16[p] = static_cast<uint16_t>(e16);
+      pair[p] = pe;
+    }
     len8[p] = static_cast<uint8_t>(e8);
     run8[p] = static_cast<uint8_t>(r8);
   }
@@ -248,7 +266,7 @@ cudaError_t launch_prepare(const PrepParams& p, cudaStream_t stream) {
 }
 
 size_t table_bytes(uint32_t K, uint32_t alphabet) {
-  const size_t b = table_sub_off(K, alphabet) + 2 * static_cast<size_t>(kSubCap);
+  const size_t b = table_pair_off(K, alphabet) + (static_cast<size_t>(4) << K);
   return (b + 255) & ~static_cast<size_t>(255);
 }
 

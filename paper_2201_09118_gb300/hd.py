@@ -127,7 +127,7 @@ _SIGS = {
     "hd_decode": ([_P, ctypes.POINTER(hd_field), _P, _P], ctypes.c_int),
     "hd_status": ([_P, _P], ctypes.c_int),
     "hd_sync_points": ([_P, ctypes.POINTER(hd_field), _P, _P], ctypes.c_int),
-    "hd_inspect_tables": ([_P, _P, ctypes.c_uint32, ctypes.c_uint32, _P, _P, _P, _P],
+    "hd_inspect_tables": ([_P, _P, ctypes.c_uint32, ctypes.c_uint32, _P, _P, _P, _P, _P],
                           ctypes.c_int),
     "hd_decode_batch": ([_P, ctypes.POINTER(hd_field), ctypes.c_uint32, _P, _P], ctypes.c_int),
     "hd_batch_status": ([_P, _P, ctypes.c_uint32, _P], ctypes.c_int),
@@ -351,16 +351,18 @@ class Context:
 
     def inspect_tables(self, lengths_dev, alphabet: int, K: int, stream=None) -> dict:
         """The per-prefix decode tables (hd_inspect_tables) of the code-length
-        table `lengths_dev` (a uint8 device tensor): numpy arrays lut16, len8
-        and run8 of 2^K entries each."""
+        table `lengths_dev` (a uint8 device tensor): numpy arrays lut16, len8,
+        run8 and pair of 2^K entries each."""
         n = 1 << K
         lut16 = np.zeros(n, np.uint16)
         len8 = np.zeros(n, np.uint8)
         run8 = np.zeros(n, np.uint8)
+        pair = np.zeros(n, np.uint32)
         _check("hd_inspect_tables", self._lib.hd_inspect_tables(
             self.handle, ctypes.c_void_p(lengths_dev.data_ptr()), alphabet, K,
-            lut16.ctypes.data, len8.ctypes.data, run8.ctypes.data, _stream_handle(stream)))
-        return {"lut16": lut16, "len8": len8, "run8": run8}
+            lut16.ctypes.data, len8.ctypes.data, run8.ctypes.data, pair.ctypes.data,
+            _stream_handle(stream)))
+        return {"lut16": lut16, "len8": len8, "run8": run8, "pair": pair}
 
     def decode_batch(self, fields: Sequence[DeviceField], outs, stream=None) -> None:
         nf = len(fields)

@@ -404,6 +404,33 @@ def test_pre_filled_windows_of_1bit_runs(ctx, case, with_gap, S, threads, window
     assert np.all(r[3 + c["n"]:] == np.uint16(CANARY))
 
 
+@pytest.mark.parametrize("A,scale", [(1024, 1.0), (256, 2.5), (4096, 1.5)])
+@pytest.mark.parametrize("with_gap", [True, False], ids=["gap", "selfsync"])
+@pytest.mark.parametrize("S,threads,window", [(64, 128, 0), (128, 512, 512), (256, 256, 0),
+                                              (128, 128, 2048)])
+def test_two_code_lookups(ctx, A, scale, with_gap, S, threads, window):
+    # fields of 1.25 to 4 bits per code: the two-phase write kernel takes the
+    # first two codes of a first-level prefix with one lookup when both lie
+    # within it (alphabets up to 1024; a 4096-symbol field keeps one code per
+    # lookup), the window in several passes, the output at an odd offset
+    x = synth.laplace_codes(600001, scale=scale, center=A // 2, alphabet=A, seed=A + S + threads)
+    c = oracle.compress(x, A, S=S if S < 256 else 128)
+    bits = c["nbits"] / c["n"]
+    assert 1.25 <= bits < 4.0, bits
+    f = dev_field(c, with_gap)
+    buf = torch.full((c["n"] + 40,), CANARY, dtype=torch.int32).to(torch.int16).cuda()
+    ctx.set_config(decoder=1 if with_gap else 0, subseq_bits=S, threads=threads, window=window)
+    try:
+        ctx.decode(f, buf[5:])
+        assert ctx.status() == 0
+    finally:
+        ctx.reset_config()
+    r = buf.cpu().numpy().view(np.uint16)
+    assert np.all(r[:5] == np.uint16(CANARY))
+    assert np.array_equal(r[5:5 + c["n"]], x)
+    assert np.all(r[5 + c["n"]:] == np.uint16(CANARY))
+
+
 # ---------------------------------------------------------------------------
 # full-size workload: the 512^3 field of Lorenzo codes
 # ---------------------------------------------------------------------------

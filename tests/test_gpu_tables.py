@@ -6,7 +6,9 @@ themselves from the oracle's RFC 1951 assignment, pinned in test_oracle.py).
 For every K-bit prefix p the expected entries follow from the codes alone:
   * a code of at most K bits that p starts with: its length and symbol; the
     run entry counts the codes that lie wholly within p's K bits, decoded one
-    after another (at most 7), and the bits they take;
+    after another (at most 7), and the bits they take; the two-code entry
+    holds the first two of them when there are two and the alphabet's
+    symbols fit 10 bits;
   * otherwise the codes longer than K bits that start with p: the shortest
     length, and whether the prefix is "mixed" (codes of several lengths under
     it, or windows under it that are no code); no code at all reads as 33.
@@ -51,6 +53,8 @@ def expected_tables(lengths, K):
     lut16 = np.zeros(n, np.uint16)
     len8 = np.zeros(n, np.uint8)
     run8 = np.zeros(n, np.uint8)
+    pair = np.zeros(n, np.uint32)
+    A = lengths.size
 
     def code_at(p, used):
         # the code of at most K - used bits at bit offset `used` of prefix p
@@ -68,13 +72,21 @@ def expected_tables(lengths, K):
             lut16[p] = (L << 12) | (s & 0xFFF)
             len8[p] = L
             used, m = L, 1
+            second = None
             while m < 7 and used < K:
                 nxt = code_at(p, used)
                 if nxt is None:
                     break
+                if m == 1:
+                    second = nxt
                 used += nxt[0]
                 m += 1
             run8[p] = (m << 4) | used
+            if second is not None and A <= 1024:
+                pair[p] = ((2 << 30) | (L << 26) | (second[0] << 22) | ((second[1] & 0x3FF) << 10)
+                           | (s & 0x3FF))
+            else:
+                pair[p] = (1 << 30) | (L << 26) | (s & 0xFFF)
         else:
             ls = long_by_prefix.get(p, [])
             if not ls:
@@ -86,7 +98,8 @@ def expected_tables(lengths, K):
             lut16[p] = lmin | (MIXED16 if mixed else 0)
             len8[p] = (WALK8 | lmin) if mixed else lmin
             run8[p] = 0
-    return {"lut16": lut16, "len8": len8, "run8": run8}
+            pair[p] = lut16[p]
+    return {"lut16": lut16, "len8": len8, "run8": run8, "pair": pair}
 
 
 def fibonacci_lengths():
@@ -119,6 +132,10 @@ CODEBOOKS = {
         .astype(np.uint64)),
     # an incomplete code (one used symbol: Kraft sum 1/2): prefixes with no code
     "one_symbol": lambda: np.array([0, 0, 1, 0, 0, 0, 0, 0], np.uint8),
+    # 4096 symbols: symbols past 10 bits, so no two-code entries
+    "wide4096": lambda: oracle.code_lengths(
+        oracle.histogram(synth.laplace_codes(300000, scale=3.0, center=2048, alphabet=4096,
+                                             seed=5), 4096).astype(np.uint64)),
 }
 
 
@@ -130,7 +147,7 @@ def test_tables_match_the_canonical_codes(ctx, book, K):
     dev = torch.from_numpy(np.ascontiguousarray(lengths)).cuda()
     got = ctx.inspect_tables(dev, A, K)
     want = expected_tables(lengths, K)
-    for name in ("lut16", "len8", "run8"):
+    for name in ("lut16", "len8", "run8", "pair"):
         bad = np.nonzero(got[name] != want[name])[0]
         assert bad.size == 0, (name, [(int(p), int(got[name][p]), int(want[name][p]))
                                       for p in bad[:6]])
