@@ -297,10 +297,13 @@ int prepare_launch(const hd_ctx* c, std::vector<FieldDesc>& descs, const hd::Lau
   hd::LaunchShape s = shape;
   uint64_t bits = 0, syms = 0;
   uint32_t amax = 0;
+  uint64_t syms_long = 0;  // symbols of fields of 4 or more bits per code
   for (auto& d : descs) {
     bits += d.nbits;
     syms += d.n;
     amax = std::max(amax, d.alphabet);
+    if (static_cast<double>(d.nbits) >= kRunsBelowBits * static_cast<double>(d.n))
+      syms_long += d.n;
   }
   const double bits_per = static_cast<double>(bits) / static_cast<double>(syms ? syms : 1);
   // symbols of codes longer than the first-level table, kept in shared memory
@@ -309,11 +312,13 @@ int prepare_launch(const hd_ctx* c, std::vector<FieldDesc>& descs, const hd::Lau
   // 16-bit first-level entries when every field's symbols fit 12 bits
   s.lut16 = hd::lut16_usable(s.K, amax) ? 1u : 0u;
   // run table for counting when codes are short (measured: +24% decode at
-  // 1.9 bits per code, -6% at 9 bits), and there two codes per lookup in the
-  // decode-and-write kernel (fields under 1.25 bits write runs instead)
-  s.runs = bits_per < kZeroRunsBelowBits ? 3u
-           : bits_per < kRunsBelowBits   ? (1u | hd::kShapePairs)
-                                         : 0u;
+  // 1.9 bits per code, -6% at 9 bits); two codes per lookup in the
+  // decode-and-write kernel when fields of 4+ bits per code hold under a
+  // quarter of the launch's symbols (their prefixes rarely hold two codes, and
+  // the batched workload, about half of them, decoded 3% slower with it);
+  // fields under 1.25 bits write runs instead
+  const uint32_t pairs = 4 * syms_long < syms ? hd::kShapePairs : 0u;
+  s.runs = bits_per < kZeroRunsBelowBits ? 3u : bits_per < kRunsBelowBits ? (1u | pairs) : 0u;
   if (s.window == 0) {
     // output window: about 1.2x a tile's expected symbol count, rounded up to
     // a multiple of 2048 so that batches of similar code lengths share a shape

@@ -18,6 +18,8 @@
 //                closes the last open subsequence.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "common.cuh"
 #include "decode_common.cuh"
 #include "kernels.h"
@@ -163,26 +165,35 @@ __global__ void __launch_bounds__(kEncThreads) k_enc_write(const __grid_constant
       if (E.gap) {
         // gap[j] for every subsequence boundary j*S in (previous start, start]
         // of one of this thread's codewords; the end of the stream closes the
-        // last subsequence
-        uint64_t prev = 0;
+        // last subsequence.  Positions are taken relative to the start of the
+        // subsequence holding the thread's first codeword (32-bit arithmetic:
+        // the thread's codewords span at most 16 * 32 bits).
+        const uint64_t j0 = off0 >> lgS;
+        const uint64_t sub0 = j0 << lgS;
+        const uint64_t nrel = E.nsub > j0 ? E.nsub - j0 : 0;  // subsequences from j0 on
+        const uint32_t jmax = nrel < 0xFFFFFFFFull ? static_cast<uint32_t>(nrel) : 0xFFFFFFFFu;
+        uint32_t r = static_cast<uint32_t>(off0 - sub0);
+        int32_t rprev = INT32_MIN;  // the stream's first codeword opens subsequence 0
         if (i0 > 0) {
           const uint32_t xp = __ldg(E.codes + i0 - 1);
-          prev = off0 - (xp < E.alphabet ? lens[xp] : 0u);
+          rprev = static_cast<int32_t>(r) - static_cast<int32_t>(xp < E.alphabet ? lens[xp] : 0u);
         }
-        uint64_t off = off0;
+        // index of the stream's last codeword among the thread's, if it holds it
+        const uint32_t klast = E.n > i0 && E.n - i0 <= kEncPer ? static_cast<uint32_t>(E.n - i0 - 1)
+                                                              : 0xFFFFFFFFu;
 #pragma unroll
         for (int k = 0; k < kEncPer; ++k) {
           const uint32_t L = len[k];
           if (L) {
-            const uint64_t j = off >> lgS;
-            if ((i0 + k == 0 || (j << lgS) > prev) && j < E.nsub)
-              E.gap[j] = static_cast<uint8_t>(off - (j << lgS));
-            prev = off;
-            off += L;
-            if (i0 + k + 1 == E.n) {
-              const uint64_t je = (prev >> lgS) + 1;
-              if (je < E.nsub && (je << lgS) <= off)
-                E.gap[je] = static_cast<uint8_t>(off - (je << lgS));
+            const uint32_t jr = r >> lgS;
+            const int32_t b = static_cast<int32_t>(jr << lgS);
+            if (b > rprev && jr < jmax) E.gap[j0 + jr] = static_cast<uint8_t>(r - static_cast<uint32_t>(b));
+            rprev = static_cast<int32_t>(r);
+            r += L;
+            if (static_cast<uint32_t>(k) == klast) {
+              const uint32_t je = (static_cast<uint32_t>(rprev) >> lgS) + 1;
+              if (je < jmax && (je << lgS) <= r)
+                E.gap[j0 + je] = static_cast<uint8_t>(r - (je << lgS));
             }
           }
         }
