@@ -179,15 +179,16 @@ __global__ void __launch_bounds__(kEncThreads) k_enc_write(const __grid_constant
           rprev = static_cast<int32_t>(r) - static_cast<int32_t>(xp < E.alphabet ? lens[xp] : 0u);
         }
         // index of the stream's last codeword among the thread's, if it holds it
-        const uint32_t klast = E.n > i0 && E.n - i0 <= kEncPer ? static_cast<uint32_t>(E.n - i0 - 1)
-                                                              : 0xFFFFFFFFu;
+        const uint32_t klast =
+            E.n > i0 && E.n - i0 <= kEncPer ? static_cast<uint32_t>(E.n - i0 - 1) : 0xFFFFFFFFu;
 #pragma unroll
         for (int k = 0; k < kEncPer; ++k) {
           const uint32_t L = len[k];
           if (L) {
             const uint32_t jr = r >> lgS;
             const int32_t b = static_cast<int32_t>(jr << lgS);
-            if (b > rprev && jr < jmax) E.gap[j0 + jr] = static_cast<uint8_t>(r - static_cast<uint32_t>(b));
+            if (b > rprev && jr < jmax)
+              E.gap[j0 + jr] = static_cast<uint8_t>(r - static_cast<uint32_t>(b));
             rprev = static_cast<int32_t>(r);
             r += L;
             if (static_cast<uint32_t>(k) == klast) {
