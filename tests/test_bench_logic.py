@@ -44,6 +44,10 @@ def test_traffic_record_is_refused_once_a_source_changes(monkeypatch):
 
 
 def test_peak_is_the_measured_copy_bandwidth():
-    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if not os.path.exists(p):
+        assert bench.measured_peak() == (bench.FALLBACK_HBM_GBS, "fallback")
+        return
+    with open(p) as f:
         d = json.load(f)
     assert bench.measured_peak() == (float(d["hbm_gbs"]), "measured")
